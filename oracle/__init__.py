@@ -1,0 +1,232 @@
+"""FP64 CPU oracle of the thin-film D2Q9 lattice Boltzmann method.
+
+Test infrastructure only.  The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The oracle shares no
+code with the CUDA library (``paper_1810_07642_gb300``), and the library never
+imports it.
+
+The arithmetic lives in ``tflbm_oracle.c`` (plain C, double precision, built
+with ``-ffp-contract=off``).  This module compiles it with gcc on first use
+and wraps it with ctypes on numpy float64 arrays.  Populations are stored as
+``f[l, y, x]`` (shape ``(9, ny, nx)``); fields are ``(ny, nx)`` with x fastest.
+The method follows Section II of Zitz et al., arXiv:1810.07642: Eqs. (speeds),
+(equilibria), (LBE), (force), (pfilm), (disjoiningP), (forcefric),
+(alphafric), (derivative) and (n_laplace).  The readings of the garbled or
+silent points are listed in the header of ``tflbm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tflbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, f"liboracle_{platform.machine()}.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library (gcc, OpenMP, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``orc_params`` in tflbm_oracle.c (same field order)."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("n_exp", ctypes.c_int32), ("m_exp", ctypes.c_int32),
+        ("pi_sign", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("g", ctypes.c_double), ("delta", ctypes.c_double),
+        ("hstar", ctypes.c_double), ("gx_body", ctypes.c_double),
+        ("gy_body", ctypes.c_double),
+    ]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int32)
+_P = ctypes.POINTER(Params)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_lattice.argtypes = [_I, _I, _D]
+        L.orc_feq.argtypes = [ctypes.c_double] * 4 + [_D]
+        L.orc_laplacian.argtypes = [ctypes.c_int32, ctypes.c_int32, _D, _D]
+        L.orc_gradient.argtypes = [ctypes.c_int32, ctypes.c_int32, _D, _D, _D]
+        L.orc_kappa.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
+        L.orc_kappa.restype = ctypes.c_double
+        L.orc_kappa_field.argtypes = [_P, _D, _D]
+        L.orc_fdisj.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
+        L.orc_fdisj.restype = ctypes.c_double
+        L.orc_alpha.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_alpha.restype = ctypes.c_double
+        L.orc_moments.argtypes = [_P, _D, _D, _D, _D]
+        L.orc_pressure_force.argtypes = [_P, _D, _D, _D, _D, _D]
+        L.orc_init.argtypes = [_P, _D, _D]
+        L.orc_step.argtypes = [_P, _D, _D, ctypes.c_int64]
+        L.orc_mass.argtypes = [_P, _D]
+        L.orc_mass.restype = ctypes.c_double
+        L.orc_num_threads.restype = ctypes.c_int32
+        L.orc_set_num_threads.argtypes = [ctypes.c_int32]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+@dataclass
+class Config:
+    """Physical parameters of one run (lattice units, dx = dt = 1)."""
+    nx: int
+    ny: int
+    tau: float = 1.0
+    gamma: float = 0.01
+    g: float = 0.0
+    delta: float = 1.0
+    hstar: float = 0.07
+    n_exp: int = 3
+    m_exp: int = 2
+    pi_sign: int = 1
+    gx_body: float = 0.0
+    gy_body: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+    def cparams(self) -> Params:
+        return Params(self.nx, self.ny, self.n_exp, self.m_exp, self.pi_sign, 0,
+                      self.tau, self.gamma, self.g, self.delta, self.hstar,
+                      self.gx_body, self.gy_body)
+
+
+def lattice():
+    """Velocities c_l (Eq. speeds) and weights w_l as (cx, cy, w)."""
+    cx = np.zeros(9, np.int32)
+    cy = np.zeros(9, np.int32)
+    w = np.zeros(9)
+    lib().orc_lattice(cx.ctypes.data_as(_I), cy.ctypes.data_as(_I), _ptr(w))
+    return cx, cy, w
+
+
+def feq(g: float, h: float, ux: float, uy: float) -> np.ndarray:
+    out = np.zeros(9)
+    lib().orc_feq(g, h, ux, uy, _ptr(out))
+    return out
+
+
+def laplacian(phi: np.ndarray) -> np.ndarray:
+    phi = np.ascontiguousarray(phi, np.float64)
+    out = np.empty_like(phi)
+    lib().orc_laplacian(phi.shape[1], phi.shape[0], _ptr(phi), _ptr(out))
+    return out
+
+
+def gradient(phi: np.ndarray):
+    phi = np.ascontiguousarray(phi, np.float64)
+    gx = np.empty_like(phi)
+    gy = np.empty_like(phi)
+    lib().orc_gradient(phi.shape[1], phi.shape[0], _ptr(phi), _ptr(gx), _ptr(gy))
+    return gx, gy
+
+
+def kappa(theta: float, n: int, m: int, hstar: float) -> float:
+    return lib().orc_kappa(theta, n, m, hstar)
+
+
+def kappa_field(cfg: Config, theta) -> np.ndarray:
+    theta = np.broadcast_to(np.asarray(theta, np.float64), (cfg.ny, cfg.nx))
+    theta = np.ascontiguousarray(theta)
+    out = np.empty_like(theta)
+    p = cfg.cparams()
+    lib().orc_kappa_field(ctypes.byref(p), _ptr(theta), _ptr(out))
+    return out
+
+
+def fdisj(h: float, n: int, m: int, hstar: float) -> float:
+    return lib().orc_fdisj(h, n, m, hstar)
+
+
+def alpha(h: float, delta: float) -> float:
+    return lib().orc_alpha(h, delta)
+
+
+def init(cfg: Config, h0: np.ndarray) -> np.ndarray:
+    """Post-streaming populations at t = 0: f_l = f_eq_l(h0, u = 0)."""
+    h0 = np.ascontiguousarray(h0, np.float64)
+    assert h0.shape == (cfg.ny, cfg.nx)
+    f = np.empty((9, cfg.ny, cfg.nx))
+    p = cfg.cparams()
+    lib().orc_init(ctypes.byref(p), _ptr(h0), _ptr(f))
+    return f
+
+
+def step(cfg: Config, kap: np.ndarray, f: np.ndarray, nsteps: int) -> np.ndarray:
+    """Advance f (modified in place and returned) by nsteps of Eq. (LBE)."""
+    assert f.shape == (9, cfg.ny, cfg.nx) and f.dtype == np.float64 and f.flags.c_contiguous
+    kap = np.ascontiguousarray(np.broadcast_to(np.asarray(kap, np.float64), (cfg.ny, cfg.nx)))
+    p = cfg.cparams()
+    lib().orc_step(ctypes.byref(p), _ptr(kap), _ptr(f), int(nsteps))
+    return f
+
+
+def moments(cfg: Config, f: np.ndarray):
+    """(h, ux, uy) of the post-streaming populations f."""
+    h = np.empty((cfg.ny, cfg.nx))
+    ux = np.empty_like(h)
+    uy = np.empty_like(h)
+    p = cfg.cparams()
+    lib().orc_moments(ctypes.byref(p), _ptr(f), _ptr(h), _ptr(ux), _ptr(uy))
+    return h, ux, uy
+
+
+def pressure_force(cfg: Config, kap: np.ndarray, f: np.ndarray):
+    """(p_film, Fx, Fy) of the post-streaming populations f."""
+    kap = np.ascontiguousarray(np.broadcast_to(np.asarray(kap, np.float64), (cfg.ny, cfg.nx)))
+    pf = np.empty((cfg.ny, cfg.nx))
+    fx = np.empty_like(pf)
+    fy = np.empty_like(pf)
+    p = cfg.cparams()
+    lib().orc_pressure_force(ctypes.byref(p), _ptr(kap), _ptr(f), _ptr(pf), _ptr(fx), _ptr(fy))
+    return pf, fx, fy
+
+
+def mass(cfg: Config, f: np.ndarray) -> float:
+    p = cfg.cparams()
+    return lib().orc_mass(ctypes.byref(p), _ptr(f))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(int(n))
+
+
+def run(cfg: Config, h0: np.ndarray, theta, nsteps: int):
+    """Convenience: init from h0, advance nsteps, return (f, h, ux, uy)."""
+    kap = kappa_field(cfg, theta)
+    f = init(cfg, h0)
+    step(cfg, kap, f, nsteps)
+    h, ux, uy = moments(cfg, f)
+    return f, h, ux, uy

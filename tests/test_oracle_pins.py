@@ -1,0 +1,429 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the moment
+constraints the paper imposes on the equilibria, textbook stencil properties,
+the contact-angle condition behind kappa, closed forms of special cases, an
+exact linearisation of the scheme derived by hand, the paper's printed
+critical wavenumbers, symmetries, and a brute-force literal evaluation of
+Eq. (LBE) on tiny lattices.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+from paper_1810_07642_gb300 import inputs
+import linear_theory as LT
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def cfg_of(p, **over):
+    d = {k: v for k, v in p.items() if k in O.Config.__dataclass_fields__}
+    d.update(over)
+    return O.Config(**d)
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _threads():
+    O.set_num_threads(min(8, os.cpu_count() or 1))
+    yield
+
+
+# --------------------------------------------------------------- lattice
+
+def test_velocity_set_is_eq_speeds():
+    """Eq. (speeds): rest, then angles (l-1) pi/4; odd l axis, even l diagonal."""
+    cx, cy, w = O.lattice()
+    expect = [(0, 0), (1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    assert list(zip(cx.tolist(), cy.tolist())) == expect
+    assert np.allclose(w, [4 / 9] + [1 / 9 if l % 2 else 1 / 36 for l in range(1, 9)], rtol=0, atol=0)
+
+
+def test_weights_isotropy():
+    """D2Q9 lattice tensors up to fourth order (c_s^2 = 1/3)."""
+    cx, cy, w = O.lattice()
+    c = np.stack([cx, cy], 1).astype(float)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(w @ c, 0, atol=1e-16)
+    assert np.allclose(np.einsum("l,li,lj->ij", w, c, c), np.eye(2) / 3, atol=1e-16)
+    assert np.allclose(np.einsum("l,li,lj,lk->ijk", w, c, c, c), 0, atol=1e-16)
+    d = np.eye(2)
+    iso4 = (np.einsum("ij,kl->ijkl", d, d) + np.einsum("ik,jl->ijkl", d, d)
+            + np.einsum("il,jk->ijkl", d, d)) / 9
+    assert np.allclose(np.einsum("l,li,lj,lk,lm->ijkm", w, c, c, c, c), iso4, atol=1e-16)
+
+
+# ----------------------------------------------------------- equilibrium
+
+def test_equilibrium_meets_moment_constraints():
+    """Section II: sum f_eq = h, sum c f_eq = h u,
+    sum c_i c_j f_eq = g h^2 / 2 delta_ij + h u_i u_j."""
+    cx, cy, _ = O.lattice()
+    c = np.stack([cx, cy], 1).astype(float)
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        g = rng.uniform(-1e-3, 1e-3)
+        h = rng.uniform(0.05, 20)
+        u = rng.uniform(-0.1, 0.1, 2)
+        f = O.feq(g, h, u[0], u[1])
+        assert abs(f.sum() - h) <= 1e-14 * h
+        assert np.allclose(c.T @ f, h * u, rtol=0, atol=1e-14 * h)
+        flux = np.einsum("l,li,lj->ij", f, c, c)
+        expect = 0.5 * g * h * h * np.eye(2) + h * np.outer(u, u)
+        assert np.allclose(flux, expect, rtol=0, atol=1e-13 * h)
+
+
+def test_equilibrium_at_rest_without_gravity_is_all_rest():
+    f = O.feq(0.0, 1.7, 0.0, 0.0)
+    assert f[0] == 1.7 and np.all(f[1:] == 0)
+
+
+# -------------------------------------------------------------- stencils
+
+def _quadratic(nx, ny, a, b, c, d, e, f_):
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    return a + b * x + c * y + d * x * x + e * x * y + f_ * y * y, x, y
+
+
+def test_laplacian_exact_on_quadratics():
+    """A consistent 9-point Laplacian is exact on quadratic polynomials
+    (checked away from the periodic seam)."""
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        a, b, c, d, e, f_ = rng.normal(size=6)
+        phi, _, _ = _quadratic(20, 17, a, b, c, d, e, f_)
+        lap = O.laplacian(phi)[1:-1, 1:-1]
+        assert np.allclose(lap, 2 * d + 2 * f_, rtol=0, atol=1e-11)
+
+
+def test_laplacian_fourier_symbol_isotropic():
+    """Symbol -k^2 + k^4/12 + O(k^6) in every direction; constants map to 0."""
+    n = 240
+    assert np.abs(O.laplacian(np.full((8, 8), 3.25))).max() < 1e-14
+    for (mx, my) in [(3, 0), (0, 3), (2, 2), (4, 3)]:
+        kx, ky = 2 * math.pi * mx / n, 2 * math.pi * my / n
+        y, x = np.mgrid[0:n, 0:n].astype(float)
+        phi = np.cos(kx * x + ky * y + 0.3)
+        ratio = (O.laplacian(phi) * phi).sum() / (phi * phi).sum()
+        k2 = kx * kx + ky * ky
+        assert abs(ratio - (-k2 + k2 * k2 / 12)) < 5 * k2 ** 3 / 360 + 1e-13
+
+
+def test_gradient_exact_on_quadratics():
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        a, b, c, d, e, f_ = rng.normal(size=6)
+        phi, x, y = _quadratic(19, 21, a, b, c, d, e, f_)
+        gx, gy = O.gradient(phi)
+        s = (slice(1, -1), slice(1, -1))
+        assert np.allclose(gx[s], (b + 2 * d * x + e * y)[s], rtol=0, atol=1e-11)
+        assert np.allclose(gy[s], (c + e * x + 2 * f_ * y)[s], rtol=0, atol=1e-11)
+
+
+# ------------------------------------------------------ forces, kappa
+
+@pytest.mark.parametrize("n,m,theta_deg,hstar", [(3, 2, 20, 0.07), (3, 9, 40, 0.05),
+                                                 (9, 3, 10, 0.1), (4, 10, 30, 0.07)])
+def test_kappa_gives_contact_angle_energy(n, m, theta_deg, hstar):
+    """Young's law in the disjoining form: the interface potential depth,
+    int_{h*}^inf kappa f(h) dh, equals -(1 - cos theta) (per unit gamma);
+    f(h*) = 0 and Pi is symmetric under n <-> m."""
+    th = math.radians(theta_deg)
+    kap = O.kappa(th, n, m, hstar)
+    val, _ = integrate.quad(lambda h: kap * O.fdisj(h, n, m, hstar), hstar, np.inf,
+                            epsabs=1e-13, epsrel=1e-11, limit=200)
+    assert abs(val + (1 - math.cos(th))) < 1e-8
+    assert abs(O.fdisj(hstar, n, m, hstar)) < 1e-15
+    for h in (0.5 * hstar, 2 * hstar, 10 * hstar):
+        a = O.kappa(th, n, m, hstar) * O.fdisj(h, n, m, hstar)
+        b = O.kappa(th, m, n, hstar) * O.fdisj(h, m, n, hstar)
+        assert abs(a - b) <= 1e-14 * abs(a)
+
+
+def test_alpha_no_slip_limit():
+    """delta = 0: alpha = 3/h, the no-slip lubrication mobility h^3/(3 mu)."""
+    for h in (0.07, 0.5, 1.0, 7.0):
+        assert abs(O.alpha(h, 0.0) - 3.0 / h) < 1e-15 * 3 / h
+        assert O.alpha(h, 1.0) < O.alpha(h, 0.5) < O.alpha(h, 0.0)
+
+
+# ------------------------------------------------ whole-step invariants
+
+def test_flat_film_stays_flat():
+    """Uniform h, uniform theta, no body force: nothing can move."""
+    cfg = O.Config(nx=12, ny=10, tau=0.8, g=-1e-4, delta=1.0)
+    h0 = np.full((10, 12), 1.3)
+    kap = O.kappa_field(cfg, math.radians(25))
+    f = O.init(cfg, h0)
+    f0 = f.copy()
+    O.step(cfg, kap, f, 200)
+    h, ux, uy = O.moments(cfg, f)
+    # every node does identical arithmetic, so the film stays exactly uniform;
+    # only rounding of sum_l f_eq = h lets the populations drift, by ulps
+    assert np.ptp(h) == 0 and np.ptp(f, axis=(1, 2)).max() == 0
+    assert np.abs(f - f0).max() < 1e-12
+    assert np.abs(ux).max() < 1e-14 and np.abs(uy).max() < 1e-14
+
+
+def test_mass_conservation():
+    h0, th, p = inputs.small_random(40, 36, seed=5, amp=0.2)
+    cfg = cfg_of(p, tau=0.9, gx_body=1e-5, gy_body=-3e-6, g=1e-4)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    m0 = O.mass(cfg, f)
+    assert abs(m0 - h0.sum()) < 1e-12 * m0
+    O.step(cfg, kap, f, 300)
+    assert abs(O.mass(cfg, f) - m0) < 1e-13 * m0
+
+
+@pytest.mark.parametrize("tau,delta", [(1.0, 0.0), (0.9, 0.5), (1.3, 2.0)])
+def test_uniform_film_body_force_closed_form(tau, delta):
+    """Uniform film under F = h g_par: momentum after collision is h u + F and
+    streaming leaves a uniform field alone, so
+    u_{n+1} = u_n (1 - nu alpha / h) + g_par exactly."""
+    hh, gx, gy = 1.5, 1e-5, -2e-5
+    cfg = O.Config(nx=6, ny=5, tau=tau, delta=delta, gx_body=gx, gy_body=gy, g=2e-4)
+    f = O.init(cfg, np.full((5, 6), hh))
+    kap = O.kappa_field(cfg, math.radians(30))
+    nu = (tau - 0.5) / 3
+    r = 1 - nu * LT.alpha(hh, delta) / hh
+    for nstep in range(1, 61):
+        O.step(cfg, kap, f, 1)
+        _, ux, uy = O.moments(cfg, f)
+        for g_, u in ((gx, ux), (gy, uy)):
+            expect = g_ * hh / (nu * LT.alpha(hh, delta)) * (1 - r ** nstep)
+            assert np.allclose(u, expect, rtol=1e-11, atol=1e-18)
+
+
+# ------------------------------------------- linear stability (RT, Pi)
+
+def _mode_growth(cfg, kap, h0, k, steps, every, skip):
+    f = O.init(cfg, h0)
+    x = np.arange(cfg.nx)
+    e = np.exp(-1j * k * x)
+    ts, la = [], []
+    for s in range(0, steps + 1, every):
+        if s:
+            O.step(cfg, kap, f, every)
+        h, _, _ = O.moments(cfg, f)
+        ts.append(s)
+        la.append(math.log(abs((h[0] - h[0].mean()) @ e)))
+    ts, la = np.array(ts), np.array(la)
+    sel = ts >= skip
+    return np.polyfit(ts[sel], la[sel], 1)[0]
+
+
+@pytest.mark.parametrize("mode,tau,delta", [(1, 1.0, 0.0), (2, 1.0, 0.0), (3, 1.0, 0.0),
+                                            (1, 0.8, 0.0), (3, 1.2, 1.0)])
+def test_rayleigh_taylor_matches_linearised_scheme(mode, tau, delta):
+    """Hanging film (g < 0), gamma = 0.01, 128 x 2 (the mode is 1D): the
+    fitted growth rate equals the dominant eigenvalue of the hand-linearised
+    step (unstable modes below k_c, damped above)."""
+    h0, th, p = inputs.rayleigh_taylor(128, ny=2, mode=mode, g=-1e-4)
+    cfg = cfg_of(p, tau=tau, delta=delta)
+    k = 2 * math.pi * mode / 128
+    sig = _mode_growth(cfg, O.kappa_field(cfg, th), h0, k, 12000, 1000, 2000)
+    ref = LT.scheme_growth_rate(k, 1.0, -1e-4, 0.01, tau, delta)
+    assert abs(sig - ref) <= 1e-4 * abs(ref)
+
+
+def test_rayleigh_taylor_continuum_limit():
+    """Eq. (RTgrowth) with the viscous terms of Eq. (hydro2): the scheme
+    approaches it as the per-step friction rate lambda = nu alpha / h -> 0;
+    the explicit friction makes the gravity term first-order in lambda, so
+    the deviation must stay within lambda |g / (g + gamma k^2)|."""
+    for h0amp, mode, nx in [(3.0, 1, 128), (2.0, 1, 192)]:
+        h0, th, p = inputs.rayleigh_taylor(nx, ny=2, mode=mode, g=-1e-4)
+        cfg = cfg_of(p)
+        k = 2 * math.pi * mode / nx
+        sig = _mode_growth(cfg, O.kappa_field(cfg, th), h0 * h0amp, k, 12000, 1000, 2000)
+        lub = LT.lubrication_growth_rate(k, h0amp, -1e-4, 0.01, 1.0, 0.0)
+        lam = (1 / 6) * 3 / h0amp ** 2
+        bound = lam * abs(1e-4 / (-1e-4 + 0.01 * k * k))
+        assert sig > 0 and abs(sig / lub - 1) <= bound
+        plain = LT.rt_growth_rate(k, h0amp, 1e-4, 0.01, 1 / 6)
+        assert abs(lub / plain - 1) <= 3 * (k * h0amp) ** 2
+
+
+def test_golden_rt_critical_wavenumber():
+    """Section III A prints k_c = 0.06 .. 0.09 for |g| = 4e-5 .. 8e-5 at
+    gamma = 0.01.  k_c = sqrt(|g| / gamma) must round to the printed values
+    and, in the oracle, lattice modes well below k_c grow while those above
+    decay."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "rt_critical_wavenumber.txt"))
+            if l.strip() and not l.startswith("#")]
+    for gamma, g, kc_printed in ((float(a), float(b), float(c)) for a, b, c in rows):
+        kc = math.sqrt(g / gamma)
+        assert round(kc, 2) == kc_printed
+        nx = 256
+        below = max(m for m in range(1, 20) if 2 * math.pi * m / nx < 0.75 * kc)
+        above = min(m for m in range(1, 20) if 2 * math.pi * m / nx > 1.15 * kc)
+        for mode, sign in ((below, 1), (above, -1)):
+            h0, th, p = inputs.rayleigh_taylor(nx, ny=2, mode=mode, g=-g, gamma=gamma)
+            cfg = cfg_of(p, delta=1.0)
+            k = 2 * math.pi * mode / nx
+            sig = _mode_growth(cfg, O.kappa_field(cfg, th), h0, k, 6000, 1000, 1000)
+            assert sign * sig > 0
+
+
+@pytest.mark.parametrize("pi_sign", [1, -1])
+def test_disjoining_pressure_linear_stability(pi_sign):
+    """Flat film h0 = 1 on theta = 40 deg, (n, m) = (3, 2), delta = 1: the
+    growth rate of a long mode equals the linearised scheme's, which under
+    the physical sign (p = -gamma(lap h + Pi)) is spinodal growth
+    (kappa f'(h0) > k^2) and under the printed sign is decay."""
+    nx, mode = 128, 2
+    k = 2 * math.pi * mode / nx
+    h0, th, p = inputs.rayleigh_taylor(nx, ny=2, mode=mode, g=0.0, amp=1e-4)
+    cfg = cfg_of(p, delta=1.0, pi_sign=pi_sign, hstar=0.07, n_exp=3, m_exp=2)
+    theta = math.radians(40)
+    kap = LT.kappa(theta, 3, 2, 0.07)
+    fp = LT.fdisj_prime(1.0, 3, 2, 0.07)
+    assert kap * fp > k * k
+    sig = _mode_growth(cfg, O.kappa_field(cfg, np.full_like(h0, theta)), h0, k, 6000, 500, 1000)
+    ref = LT.scheme_growth_rate(k, 1.0, 0.0, 0.01, 1.0, 1.0, kap, fp, pi_sign)
+    assert abs(sig - ref) <= 1e-4 * abs(ref)
+    assert (sig > 0) == (pi_sign == 1)
+
+
+def test_precursor_film_stable_only_under_physical_sign():
+    """A film at h = h* is the minimum of the interface potential: it is
+    linearly stable for p = -gamma(lap h + Pi), unstable for the printed sign."""
+    for pi_sign, expect_stable in ((1, True), (-1, False)):
+        k = 2 * math.pi / 32
+        kap = LT.kappa(math.radians(20), 3, 2, 0.07)
+        fp = LT.fdisj_prime(0.07, 3, 2, 0.07)
+        ref = LT.scheme_growth_rate(k, 0.07, 0.0, 0.01, 1.0, 1.0, kap, fp, pi_sign)
+        assert (ref < 0) == expect_stable
+
+
+# ----------------------------------------------------------- drop angle
+
+@pytest.mark.slow
+def test_sessile_drop_relaxes_to_equilibrium_angle():
+    """A 30-degree spherical cap on a theta = 20 deg substrate spreads to the
+    apparent angle of the disjoining-pressure model: with small slopes the
+    first integral gives tan(theta_app) = sqrt(2 (1 - cos theta)), i.e.
+    19.15 deg; the measured angle must approach [19.15, 20] deg to within
+    1 deg.  The angle is measured as in Section III B: drop volume V and apex
+    height h_d define a spherical cap (Eq. spherical_cap_vol and R(t)),
+    theta = arcsin(r / R).  Volume is conserved to rounding."""
+    rb, th0 = 30.0, math.radians(30)
+    hd = rb * math.tan(th0 / 2)
+    h0, th, p = inputs.sessile_drop(128, rb=rb, hd=hd, theta_deg=20.0, delta=1.0)
+    cfg = cfg_of(p)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+
+    def angle(h):
+        V = (h - cfg.hstar).sum()
+        hdd = h.max() - cfg.hstar
+        r2 = (6 * V / (math.pi * hdd) - hdd * hdd) / 3
+        R = (r2 + hdd * hdd) / (2 * hdd)
+        return math.degrees(math.asin(math.sqrt(r2) / R))
+
+    a0 = angle(h0)
+    O.step(cfg, kap, f, 20000)
+    h, _, _ = O.moments(cfg, f)
+    a = angle(h)
+    assert abs(h.sum() - h0.sum()) < 1e-12 * h0.sum()
+    assert a0 > 29 and 19.15 - 1 <= a <= 20 + 1, (a0, a)
+
+
+# -------------------------------------------------------------- symmetry
+
+def test_mirror_and_transpose_symmetry():
+    """A state symmetric under x -> -x and x <-> y stays symmetric."""
+    n = 24
+    rng = np.random.default_rng(7)
+    a = rng.uniform(-0.1, 0.1, (n, n))
+    a = a + a[:, (-np.arange(n)) % n]
+    a = a + a[(-np.arange(n)) % n, :]
+    a = a + a.T
+    h0 = 1 + a
+    th = np.radians(20 + 5 * (a - a.min()) / (a.max() - a.min()))
+    cfg = O.Config(nx=n, ny=n, tau=0.9, delta=1.0, g=1e-4)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    O.step(cfg, kap, f, 100)
+    h, ux, uy = O.moments(cfg, f)
+    mx = (-np.arange(n)) % n
+    scale = np.abs(h - h.mean()).max()
+    assert scale > 1e-4
+    assert np.abs(h - h[:, mx]).max() < 1e-12 * scale
+    assert np.abs(h - h.T).max() < 1e-12 * scale
+    assert np.abs(ux + ux[:, mx]).max() < 1e-12
+    assert np.abs(ux - uy.T).max() < 1e-12
+
+
+# ------------------------------------------------------------ brute force
+
+def _literal_step(nx, ny, f, P, kap):
+    """Eq. (LBE) evaluated node by node in push form, with every ingredient
+    (moments, Eq. n_laplace, Eq. pfilm, Eq. derivative, Eq. force) recomputed
+    on demand from the populations.  Slow on purpose; tiny lattices only."""
+    c = [(0, 0), (1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    w = [4 / 9, 1 / 9, 1 / 36, 1 / 9, 1 / 36, 1 / 9, 1 / 36, 1 / 9, 1 / 36]
+    nu = (P["tau"] - 0.5) / 3
+    om = 1 / P["tau"]
+
+    def H(x, y):
+        return sum(f[l][y % ny][x % nx] for l in range(9))
+
+    def U(x, y):
+        hh = H(x, y)
+        return (sum(c[l][0] * f[l][y % ny][x % nx] for l in range(9)) / hh,
+                sum(c[l][1] * f[l][y % ny][x % nx] for l in range(9)) / hh)
+
+    def lap(x, y):
+        ax = sum(H(x + c[l][0], y + c[l][1]) for l in (1, 3, 5, 7))
+        dg = sum(H(x + c[l][0], y + c[l][1]) for l in (2, 4, 6, 8))
+        return (4 * ax + dg - 20 * H(x, y)) / 6
+
+    def pf(x, y):
+        hh = H(x, y)
+        r = P["hstar"] / hh
+        Pi = kap[y % ny][x % nx] * (r ** P["n_exp"] - r ** P["m_exp"])
+        return -P["gamma"] * (lap(x, y) + P["pi_sign"] * Pi)
+
+    out = [[[0.0] * nx for _ in range(ny)] for _ in range(9)]
+    for y in range(ny):
+        for x in range(nx):
+            hh = H(x, y)
+            ux, uy = U(x, y)
+            gpx = 3 * sum(w[l] * c[l][0] * pf(x + c[l][0], y + c[l][1]) for l in range(9))
+            gpy = 3 * sum(w[l] * c[l][1] * pf(x + c[l][0], y + c[l][1]) for l in range(9))
+            al = 6 * hh / (2 * hh * hh + 6 * P["delta"] * hh + 3 * P["delta"] ** 2)
+            Fx = -hh * gpx - nu * al * ux + hh * P["gx_body"]
+            Fy = -hh * gpy - nu * al * uy + hh * P["gy_body"]
+            usq = ux * ux + uy * uy
+            g = P["g"]
+            for l in range(9):
+                cu = c[l][0] * ux + c[l][1] * uy
+                if l == 0:
+                    fe = hh - 5 * g * hh * hh / 6 - 2 * hh * usq / 3
+                elif l % 2:
+                    fe = g * hh * hh / 6 + hh * cu / 3 + hh * cu * cu / 2 - hh * usq / 6
+                else:
+                    fe = g * hh * hh / 24 + hh * cu / 12 + hh * cu * cu / 8 - hh * usq / 24
+                new = (1 - om) * f[l][y][x] + om * fe + 3 * w[l] * (c[l][0] * Fx + c[l][1] * Fy)
+                out[l][(y + c[l][1]) % ny][(x + c[l][0]) % nx] = new
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 5), (5, 3)])
+def test_bruteforce_literal_equation_tiny(nx, ny):
+    h0, th, p = inputs.small_random(nx, ny, seed=11, amp=0.3)
+    p.update(tau=0.85, g=-2e-4, gx_body=3e-5, gy_body=1e-5, delta=0.7)
+    cfg = cfg_of(p)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    lit = f.tolist()
+    for _ in range(4):
+        lit = _literal_step(nx, ny, lit, p, kap.tolist())
+    O.step(cfg, kap, f, 4)
+    assert np.abs(np.array(lit) - f).max() < 1e-13
