@@ -1,0 +1,340 @@
+"""Benchmark of the fused thin-film D2Q9 step (MLUPS and fraction of HBM roofline).
+
+Workload: chemically patterned dewetting, 2048 x 2048 periodic lattice, FP32
+populations; h0 = 1 + U(-1e-2, 1e-2), theta(x) = stripes of period 256 at
+10/40 degrees plus 32 seeded discs at 10 degrees (Section III D of the paper,
+synthetic stand-in).  Its populations (2 x 151 MB) and kappa field (17 MB)
+exceed the 129 MB L2, so no L2 flush is needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {tflbm,reference}]
+
+One step = one time step of the whole lattice = one launch of the fused
+kernel.  `value` is MLUPS = nodes x steps / time / 1e6 over all ranks (each
+rank runs an independent replica: the method needs no exchange between
+independent simulations).  `--impl reference` times the FP64 CPU oracle (the
+plain restatement of the method used by the tests) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (D2Q9 thin-film step) and % of HBM roofline; adjoint/forward cost ratio"
+N_SIDE = 2048
+BYTES_PER_LU = 76  # FP32: 9 populations read + 9 written + kappa(x)
+PROFILE = os.path.join(ROOT, "profiles", "k_step_f32_patterned_2048.json")
+KERNEL_SOURCES = ["paper_1810_07642_gb300/csrc/tflbm_step.cuh",
+                  "paper_1810_07642_gb300/csrc/step_f32.cu"]
+WORKLOAD = ("chemically patterned dewetting, 2048x2048 periodic D2Q9 thin film, FP32 "
+            "populations; h0=1+U(-1e-2,1e-2); theta stripes period 256 (10/40 deg) + 32 "
+            "seeded discs (10 deg); gamma=0.01, h*=0.07, (n,m)=(3,2), tau=1, delta=1, g=0")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None, None
+    with open(PROFILE) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_hash():
+        return None, d
+    return float(d["dram_bytes_per_launch"]), d
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_cpu_baseline(budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload: whole
+    2048^2 steps from the same h0 / theta, as many as fit the budget."""
+    import oracle as O
+    from paper_1810_07642_gb300 import inputs
+    h0, th, p = inputs.patterned_dewetting(N_SIDE, seed=0)
+    cfg = O.Config(**{k: v for k, v in p.items() if k in O.Config.__dataclass_fields__})
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    t0 = time.perf_counter()
+    O.step(cfg, kap, f, 1)
+    t1 = time.perf_counter() - t0
+    n = int(max(2, min(400, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    O.step(cfg, kap, f, n)
+    dt = time.perf_counter() - t0
+    return {"value": N_SIDE * N_SIDE * n / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} full 2048x2048 steps of the FP64 oracle on the same inputs "
+                      f"({dt:.1f} s, {O.num_threads()} OpenMP threads)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
+    2048 x R periodic band of the workload, R sized to fit a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1810_07642_gb300 import inputs
+    h0, th, p = inputs.patterned_dewetting(N_SIDE, seed=0)
+    total = args.steps + args.warmup
+
+    def band(rows):
+        cfg = O.Config(**{k: v for k, v in p.items() if k in O.Config.__dataclass_fields__})
+        cfg.ny = rows
+        kap = O.kappa_field(cfg, th[:rows])
+        return cfg, kap, O.init(cfg, np.ascontiguousarray(h0[:rows]))
+
+    cfg, kap, f = band(64)
+    t0 = time.perf_counter()
+    O.step(cfg, kap, f, 2)
+    per_node = (time.perf_counter() - t0) / (2 * N_SIDE * 64)
+    rows = int(max(2, min(N_SIDE, 150.0 / total / per_node / N_SIDE)))
+    cfg, kap, f = band(rows)
+    for _ in range(args.warmup):
+        O.step(cfg, kap, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(cfg, kap, f, 1)
+    dt = time.perf_counter() - t0
+    value = N_SIDE * rows * args.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle time step on a {N_SIDE}x{rows} periodic band of "
+              f"the workload ({O.num_threads()} OpenMP threads)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tflbm(args):
+    import torch
+    from paper_1810_07642_gb300 import build, inputs
+    from paper_1810_07642_gb300.film import ThinFilm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        if world == 1 and args.gpus > 1:
+            raise SystemExit("--gpus N > 1 must be launched with torch.distributed.run")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    h0, th, p = inputs.patterned_dewetting(N_SIDE, seed=rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = ThinFilm(p, h0, th, stream=stream)
+    launch = sim.launch
+    nodes = N_SIDE * N_SIDE
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    # warm-up
+    sim.step(args.warmup)
+    stream.synchronize()
+    m0 = sim.mass()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            sim.step(1)
+            ev[i + 1].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    barrier()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t_local = total_ms / 1e3
+    t_max = t_local
+    if dist:
+        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    m1 = sim.mass()
+    status = sim.check()
+    value = world * nodes * args.steps / t_max / 1e6
+
+    # dominant kernel: the fused step, one launch per step
+    kern_s = statistics.fmean(per) / 1e3
+    achieved = BYTES_PER_LU * nodes / kern_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic, prof = profiled_traffic()
+
+    # end to end through the public API with host buffers (pinned)
+    h_host = torch.from_numpy(np.asarray(h0, np.float32)).pin_memory()
+    th_host = torch.from_numpy(np.asarray(th, np.float32)).pin_memory()
+    out_host = torch.empty((N_SIDE, N_SIDE), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        hd = h_host.to("cuda", non_blocking=True)
+        thd = th_host.to("cuda", non_blocking=True)
+        sim2 = ThinFilm(p, hd, thd, stream=stream)
+        sim2.set_launch(**launch)
+        sim2.step(args.steps)
+        hres = sim2.moments(("h",))["h"]
+        out_host.copy_(hres, non_blocking=True)
+    stream.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    sim2.close()
+    e2e = {"value": world * nodes * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": (h_host.numel() + th_host.numel()) * 4 / args.steps,
+           "d2h_bytes_per_step": out_host.numel() * 4 / args.steps,
+           "job": f"upload h0+theta, init, {args.steps} steps, download h (host wall clock)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = oracle_cpu_baseline() if world == 1 else None
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "replicas": world,
+                   "l2": "inputs larger than L2 (302 MB populations + 17 MB kappa > 129 MB): no flush",
+                   "launch": launch, "bytes_per_lu": BYTES_PER_LU},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "k_step<float,float,OMEGA1,KFIELD>",
+                     "kernel_ms": kern_s * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "mass_rel_drift": abs(m1 - m0) / m0,
+        "check_status": status,
+        "context": {"paper_gtx1080ti_fp64_2048": 404.7},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="tflbm", choices=["tflbm", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tflbm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

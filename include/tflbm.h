@@ -1,0 +1,168 @@
+/*
+ * tflbm: GB300 (sm_103a) library for the thin-film D2Q9 lattice Boltzmann
+ * method of Zitz, Scagliarini, Maddu, Darhuber and Harting, "A lattice
+ * Boltzmann method for thin liquid film hydrodynamics", arXiv:1810.07642.
+ *
+ * Plain C ABI: plain pointers and sizes, no C++ or PyTorch types.
+ *
+ * Method (Section II of the paper).  The film height h(x, y, t) is the zeroth
+ * moment of nine populations f_l on a periodic square lattice (Eq. speeds,
+ * weights w_l).  One time step is
+ *   h = sum_l f_l,  h u = sum_l c_l f_l                        (moments)
+ *   p = -gamma (lap h + pi_sign * kappa(x) f(h))               (Eqs. pfilm, disjoiningP)
+ *   F = -h grad p - nu alpha_delta(h) u + h (gx_body, gy_body) (Eqs. force, forcefric, alphafric)
+ *   f*_l = (1 - omega) f_l + omega f_eq_l(h, u) + 3 w_l c_l . F (Eq. LBE)
+ *   f_l(x + c_l, t + 1) = f*_l(x, t)                           (streaming)
+ * with lap and grad the isotropic stencils of Eqs. (n_laplace) and
+ * (derivative), nu = (tau - 1/2)/3, omega = 1/tau and
+ * kappa = (1 - cos theta)(n - 1)(m - 1)/((n - m) h_*).
+ * Readings of garbled or silent points:
+ *   - equilibria (Eq. equilibria) with the printed c_s^2 read as e^2 = 1 (the
+ *     printed form breaks the paper's own momentum constraint);
+ *   - the printed w_l inside the Laplacian sums is dropped;
+ *   - pi_sign = +1 (default) is the physical p = -gamma(lap h + Pi); -1 is the
+ *     printed p = -gamma(lap h - Pi), whose precursor film is unstable;
+ *   - F is tangential gravity on the liquid column, F = h g_par;
+ *   - initial populations are f_l = f_eq_l(h0, u = 0).
+ *
+ * Conventions for every entry point:
+ *   - Fields are contiguous row-major [ny][nx], x fastest; population arrays
+ *     are [9][ny][nx] in the order of Eq. (speeds):
+ *     (0,0) (1,0) (1,1) (0,1) (-1,1) (-1,0) (-1,-1) (0,-1) (1,-1).
+ *   - "device" pointers are CUDA device (or managed) memory on the handle's
+ *     device.  The element type of h0, theta, and of every field output is
+ *     float for TF_LBM_F32 and double for TF_LBM_F64.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls
+ *     are asynchronous on it except tf_lbm_mass and tf_lbm_check, which
+ *     synchronise it to return a host value.
+ *   - Return value: TF_LBM_OK (0) or a negative TF_LBM_ERR_* code; nothing is
+ *     thrown across the ABI.  tf_lbm_last_error gives a message.
+ *   - The library owns the population buffers and the kappa field; the
+ *     caller owns every pointer it passes in.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef TFLBM_H
+#define TFLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* storage / compute type of the populations */
+enum {
+    TF_LBM_F32 = 0, /* FP32 storage and arithmetic */
+    TF_LBM_F64 = 1  /* FP64 storage and arithmetic */
+};
+
+/* return codes */
+enum {
+    TF_LBM_OK = 0,
+    TF_LBM_ERR_ARG = -1,         /* invalid argument (message says which)  */
+    TF_LBM_ERR_CUDA = -2,        /* a CUDA runtime call failed              */
+    TF_LBM_ERR_NOMEM = -3,       /* device allocation failed                */
+    TF_LBM_ERR_NONFINITE = -4,   /* reserved: state check found bad values  */
+    TF_LBM_ERR_UNSUPPORTED = -5  /* option not built into this library      */
+};
+
+/* bits of the status word returned by tf_lbm_check */
+enum {
+    TF_LBM_STATUS_NONFINITE = 1,  /* some population or h is NaN or inf */
+    TF_LBM_STATUS_NONPOSITIVE = 2 /* some h <= 0 (Pi and alpha singular) */
+};
+
+/* Physical and numerical parameters (lattice units, dx = dt = 1). */
+typedef struct tf_lbm_params {
+    int32_t nx, ny;       /* periodic lattice size, each >= 1                   */
+    int32_t dtype;        /* TF_LBM_F32 or TF_LBM_F64                           */
+    int32_t n_exp, m_exp; /* exponents of Eq. (disjoiningP), n != m, >= 1     */
+    int32_t pi_sign;      /* +1 physical (default) or -1 printed sign of Pi     */
+    double tau;           /* relaxation time, > 1/2; omega = 1/tau             */
+    double gamma;         /* surface tension                                    */
+    double g;             /* gravity in the equilibria (g < 0: hanging film)    */
+    double delta;         /* slip length of Eq. (alphafric), >= 0               */
+    double hstar;         /* precursor thickness h_* > 0                        */
+    double gx_body;       /* tangential body acceleration: F = h (gx, gy)       */
+    double gy_body;
+    double theta_uniform; /* contact angle in radians when no theta field      */
+} tf_lbm_params;
+
+typedef struct tf_lbm_handle tf_lbm_handle;
+
+/* Kernel launch shape of the fused step (for autotuning).
+ *   block_x: CTA width in lattice columns (32, 64, 128 or 256);
+ *   rows:    lattice rows marched by one CTA (>= 1);
+ *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
+ *            otherwise an even number >= 2). */
+typedef struct tf_lbm_launch {
+    int32_t block_x;
+    int32_t rows;
+    int32_t graph_chunk;
+    int32_t reserved;
+} tf_lbm_launch;
+
+/* Create a simulation and set f_l(x, 0) = f_eq_l(h0(x), u = 0).
+ *   out:    receives the new handle (NULL on failure).
+ *   params: copied; validated (ARG error on nx, ny < 1, tau <= 1/2,
+ *           hstar <= 0, n == m, n or m < 1, delta < 0, |pi_sign| != 1,
+ *           unknown dtype).
+ *   h0:     device [ny][nx] initial film height (not retained).
+ *   theta:  device [ny][nx] contact angle theta(x) in radians, or NULL for
+ *           params->theta_uniform everywhere.  kappa(x) is computed once,
+ *           in double precision, and kept by the library.
+ * Uses the current CUDA device; allocates about 2 * 9 * ny * nx elements.
+ * Cite: Section II, Eqs. (LBE), (equilibria), (disjoiningP). */
+int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params,
+                const void* h0, const void* theta, void* stream);
+
+/* Advance the state by nsteps >= 0 time steps of Eq. (LBE) (one fused kernel
+ * launch per step, optionally replayed from a captured CUDA graph). */
+int tf_lbm_step(tf_lbm_handle* H, int64_t nsteps, void* stream);
+
+/* Write the moments of the current post-streaming populations:
+ * h = sum_l f_l and u = sum_l c_l f_l / h (Section II).  Each of h, ux, uy
+ * is a device [ny][nx] buffer or NULL to skip it. */
+int tf_lbm_moments(tf_lbm_handle* H, void* h, void* ux, void* uy, void* stream);
+
+/* Write the film pressure p (Eq. pfilm) and the total force (Eq. force) of the
+ * current state.  Each pointer is a device [ny][nx] buffer or NULL. */
+int tf_lbm_pressure_force(tf_lbm_handle* H, void* p, void* fx, void* fy, void* stream);
+
+/* Total liquid volume sum_x h(x) of the current state, accumulated in double
+ * precision with compensated summation.  Synchronises `stream`.  The paper
+ * states the method conserves mass (Section III B). */
+int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream);
+
+/* Scan the current state: *status_host = OR of TF_LBM_STATUS_* bits (0 when
+ * every population and h is finite and every h > 0).  Synchronises `stream`. */
+int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream);
+
+/* Copy the post-streaming populations f_l(x, t) out to / in from a device
+ * [9][ny][nx] buffer of the handle's dtype (checkpoint / resume). */
+int tf_lbm_get_state(tf_lbm_handle* H, void* f, void* stream);
+int tf_lbm_set_state(tf_lbm_handle* H, const void* f, void* stream);
+
+/* Number of time steps taken since init (set_state does not reset it). */
+int64_t tf_lbm_time(const tf_lbm_handle* H);
+
+/* Read or change the launch shape (see tf_lbm_launch). */
+int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out);
+int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in);
+
+/* Release everything the handle owns (waits for its device work). NULL ok. */
+void tf_lbm_destroy(tf_lbm_handle* H);
+
+/* Message of the last failed call on H (or of the last failed tf_lbm_init
+ * on this host thread when H is NULL); "" if none.  Valid until the next
+ * call on H. */
+const char* tf_lbm_last_error(const tf_lbm_handle* H);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t tf_lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFLBM_H */

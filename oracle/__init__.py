@@ -2,8 +2,7 @@
 
 Test infrastructure only.  The test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The oracle shares no
-code with the CUDA library (``paper_1810_07642_gb300``), and the library never
-imports it.
+code with the CUDA library, and the library never imports it.
 
 The arithmetic lives in ``tflbm_oracle.c`` (plain C, double precision, built
 with ``-ffp-contract=off``).  This module compiles it with gcc on first use

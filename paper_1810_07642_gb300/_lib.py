@@ -1,0 +1,165 @@
+"""ctypes binding of libtflbm (include/tflbm.h), with the same names.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  If the library has not been built, every entry point raises;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+TF_LBM_F32, TF_LBM_F64 = 0, 1
+TF_LBM_OK = 0
+TF_LBM_ERR_ARG, TF_LBM_ERR_CUDA, TF_LBM_ERR_NOMEM = -1, -2, -3
+TF_LBM_ERR_NONFINITE, TF_LBM_ERR_UNSUPPORTED = -4, -5
+TF_LBM_STATUS_NONFINITE, TF_LBM_STATUS_NONPOSITIVE = 1, 2
+
+EXPORTED = [
+    "tf_lbm_init", "tf_lbm_step", "tf_lbm_moments", "tf_lbm_pressure_force", "tf_lbm_mass",
+    "tf_lbm_check", "tf_lbm_get_state", "tf_lbm_set_state", "tf_lbm_time", "tf_lbm_get_launch",
+    "tf_lbm_set_launch", "tf_lbm_destroy", "tf_lbm_last_error", "tf_lbm_version",
+]
+
+
+class TfLbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tflbm error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """Mirror of tf_lbm_params."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dtype", ctypes.c_int32),
+        ("n_exp", ctypes.c_int32), ("m_exp", ctypes.c_int32), ("pi_sign", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("gamma", ctypes.c_double), ("g", ctypes.c_double),
+        ("delta", ctypes.c_double), ("hstar", ctypes.c_double), ("gx_body", ctypes.c_double),
+        ("gy_body", ctypes.c_double), ("theta_uniform", ctypes.c_double),
+    ]
+
+
+class Launch(ctypes.Structure):
+    """Mirror of tf_lbm_launch."""
+    _fields_ = [("block_x", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("graph_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the in-tree libtflbm; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtflbm is not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    L.tf_lbm_init.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Params), _VP, _VP, _VP]
+    L.tf_lbm_step.argtypes = [_VP, i64, _VP]
+    L.tf_lbm_moments.argtypes = [_VP, _VP, _VP, _VP, _VP]
+    L.tf_lbm_pressure_force.argtypes = [_VP, _VP, _VP, _VP, _VP]
+    L.tf_lbm_mass.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), _VP]
+    L.tf_lbm_check.argtypes = [_VP, ctypes.POINTER(i32), _VP]
+    L.tf_lbm_get_state.argtypes = [_VP, _VP, _VP]
+    L.tf_lbm_set_state.argtypes = [_VP, _VP, _VP]
+    L.tf_lbm_time.argtypes = [_VP]
+    L.tf_lbm_time.restype = i64
+    L.tf_lbm_get_launch.argtypes = [_VP, ctypes.POINTER(Launch)]
+    L.tf_lbm_set_launch.argtypes = [_VP, ctypes.POINTER(Launch)]
+    L.tf_lbm_destroy.argtypes = [_VP]
+    L.tf_lbm_destroy.restype = None
+    L.tf_lbm_last_error.argtypes = [_VP]
+    L.tf_lbm_last_error.restype = ctypes.c_char_p
+    L.tf_lbm_version.restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int, handle=None):
+    if rc != TF_LBM_OK:
+        msg = lib().tf_lbm_last_error(handle).decode(errors="replace")
+        raise TfLbmError(rc, msg)
+
+
+# ---- thin wrappers, same names as the C entry points (pointers are ints) ----
+
+def tf_lbm_init(params: Params, h0: int, theta: int | None, stream: int = 0) -> int:
+    h = _VP()
+    rc = lib().tf_lbm_init(ctypes.byref(h), ctypes.byref(params), _VP(h0), _VP(theta or 0),
+                           _VP(stream))
+    _check(rc, None)
+    return h.value
+
+
+def tf_lbm_step(handle: int, nsteps: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_step(_VP(handle), int(nsteps), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_moments(handle: int, h: int | None, ux: int | None, uy: int | None, stream: int = 0) -> None:
+    _check(lib().tf_lbm_moments(_VP(handle), _VP(h or 0), _VP(ux or 0), _VP(uy or 0),
+                                _VP(stream)), _VP(handle))
+
+
+def tf_lbm_pressure_force(handle: int, p: int | None, fx: int | None, fy: int | None,
+                          stream: int = 0) -> None:
+    _check(lib().tf_lbm_pressure_force(_VP(handle), _VP(p or 0), _VP(fx or 0), _VP(fy or 0),
+                                       _VP(stream)), _VP(handle))
+
+
+def tf_lbm_mass(handle: int, stream: int = 0) -> float:
+    m = ctypes.c_double()
+    _check(lib().tf_lbm_mass(_VP(handle), ctypes.byref(m), _VP(stream)), _VP(handle))
+    return m.value
+
+
+def tf_lbm_check(handle: int, stream: int = 0) -> int:
+    s = ctypes.c_int32()
+    _check(lib().tf_lbm_check(_VP(handle), ctypes.byref(s), _VP(stream)), _VP(handle))
+    return s.value
+
+
+def tf_lbm_get_state(handle: int, f: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_get_state(_VP(handle), _VP(f), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_set_state(handle: int, f: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_set_state(_VP(handle), _VP(f), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_time(handle: int) -> int:
+    return int(lib().tf_lbm_time(_VP(handle)))
+
+
+def tf_lbm_get_launch(handle: int) -> Launch:
+    out = Launch()
+    _check(lib().tf_lbm_get_launch(_VP(handle), ctypes.byref(out)), _VP(handle))
+    return out
+
+
+def tf_lbm_set_launch(handle: int, block_x: int, rows: int, graph_chunk: int) -> None:
+    L = Launch(block_x, rows, graph_chunk, 0)
+    _check(lib().tf_lbm_set_launch(_VP(handle), ctypes.byref(L)), _VP(handle))
+
+
+def tf_lbm_destroy(handle: int) -> None:
+    lib().tf_lbm_destroy(_VP(handle))
+
+
+def tf_lbm_last_error(handle: int | None = None) -> str:
+    return lib().tf_lbm_last_error(_VP(handle or 0)).decode(errors="replace")
+
+
+def tf_lbm_version() -> int:
+    return int(lib().tf_lbm_version())

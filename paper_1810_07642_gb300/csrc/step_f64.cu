@@ -1,0 +1,16 @@
+// FP64 instantiations of the fused step (tflbm_step.cuh).
+#include "tflbm_step.cuh"
+
+namespace tflbm {
+
+cudaError_t launch_step_f64(const double* fin, double* fout, const double* kappa, const Geom& G,
+                            const Consts<double>& C, const Shape& S, cudaStream_t st)
+{
+    switch (S.block_x) {
+        case 64: return launch_step_bx<double, double, 64>(fin, fout, kappa, G, C, S.rows, st);
+        case 128: return launch_step_bx<double, double, 128>(fin, fout, kappa, G, C, S.rows, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tflbm

@@ -1,0 +1,416 @@
+// C-ABI of the thin-film D2Q9 lattice Boltzmann library (include/tflbm.h).
+// Owns the population ping-pong buffers, the kappa field and the reduction
+// scratch; launches the fused step kernel once per time step, optionally
+// replaying a captured CUDA graph of an even number of steps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/tflbm.h"
+#include "tflbm_internal.h"
+
+using namespace tflbm;
+
+struct tf_lbm_handle {
+    tf_lbm_params p;
+    int device = 0;
+    size_t esize = 4;
+    Geom G{};
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;               // buf[cur] holds the post-collision populations of step t-1
+    void* kappa = nullptr;     // [ny][nx] or null (uniform)
+    double kappa_u = 0.0;
+    double* partials = nullptr;
+    double* result = nullptr;
+    int nmass = 0;
+    int* flag = nullptr;
+    void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
+    int64_t time = 0;
+    Shape shape{128, 64};
+    int graph_chunk = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(tf_lbm_handle* H, int code, const std::string& msg)
+{
+    if (H) H->err = msg;
+    else g_init_err = msg;
+    return code;
+}
+
+int cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(H, e == cudaErrorMemoryAllocation ? TF_LBM_ERR_NOMEM : TF_LBM_ERR_CUDA, m);
+}
+
+#define CK(H, call, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(H, e_, what); \
+    } while (0)
+
+// Device pointers only: host memory handed to a kernel would fault or read
+// the wrong memory.
+int check_dev_ptr(tf_lbm_handle* H, const void* ptr, const char* name, bool allow_null)
+{
+    if (!ptr) {
+        if (allow_null) return TF_LBM_OK;
+        return fail(H, TF_LBM_ERR_ARG, std::string(name) + " must not be NULL");
+    }
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(H, TF_LBM_ERR_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(H, TF_LBM_ERR_ARG, std::string(name) + " must be device or managed memory");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return fail(H, TF_LBM_ERR_ARG, std::string(name) + " lives on another device");
+    return TF_LBM_OK;
+}
+
+template <typename T>
+Consts<T> make_consts(const tf_lbm_handle* H)
+{
+    Consts<T> C;
+    C.gamma = T(H->p.gamma);
+    C.g = T(H->p.g);
+    C.delta = T(H->p.delta);
+    C.hstar = T(H->p.hstar);
+    C.nu6 = T(6.0 * (H->p.tau - 0.5) / 3.0);
+    C.omega = T(1.0 / H->p.tau);
+    C.gx = T(H->p.gx_body);
+    C.gy = T(H->p.gy_body);
+    C.kappa_u = T(H->kappa_u);
+    C.pi_sgn = T(H->p.pi_sign);
+    C.n_exp = H->p.n_exp;
+    C.m_exp = H->p.m_exp;
+    return C;
+}
+
+cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
+{
+    const void* fin = H->buf[from];
+    void* fout = H->buf[from ^ 1];
+    if (H->p.dtype == TF_LBM_F32)
+        return launch_step_f32((const float*)fin, (float*)fout, (const float*)H->kappa, H->G,
+                               make_consts<float>(H), H->shape, st);
+    return launch_step_f64((const double*)fin, (double*)fout, (const double*)H->kappa, H->G,
+                           make_consts<double>(H), H->shape, st);
+}
+
+void drop_graphs(tf_lbm_handle* H)
+{
+    for (auto& e : H->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+}
+
+int validate(const tf_lbm_params* p)
+{
+    char buf[256];
+    auto bad = [&](const char* m) {
+        snprintf(buf, sizeof buf, "invalid parameter: %s", m);
+        g_init_err = buf;
+        return TF_LBM_ERR_ARG;
+    };
+    if (!p) return bad("params is NULL");
+    if (p->nx < 1 || p->ny < 1) return bad("nx and ny must be >= 1");
+    if (p->ny > 65535) return bad("ny must be <= 65535");
+    if ((long long)p->nx * p->ny > (1LL << 31)) return bad("nx * ny must be <= 2^31");
+    if (p->dtype != TF_LBM_F32 && p->dtype != TF_LBM_F64) return bad("dtype must be TF_LBM_F32 or TF_LBM_F64");
+    if (!(p->tau > 0.5)) return bad("tau must be > 1/2");
+    if (!(p->hstar > 0.0)) return bad("hstar must be > 0");
+    if (!(p->delta >= 0.0)) return bad("delta must be >= 0");
+    if (p->n_exp < 1 || p->m_exp < 1 || p->n_exp > 64 || p->m_exp > 64) return bad("n_exp and m_exp must be in [1, 64]");
+    if (p->n_exp == p->m_exp) return bad("n_exp must differ from m_exp");
+    if (p->pi_sign != 1 && p->pi_sign != -1) return bad("pi_sign must be +1 or -1");
+    if (!isfinite(p->gamma) || !isfinite(p->g) || !isfinite(p->gx_body) || !isfinite(p->gy_body) ||
+        !isfinite(p->theta_uniform) || !isfinite(p->tau))
+        return bad("non-finite parameter");
+    return TF_LBM_OK;
+}
+
+Shape default_shape(const Geom& G)
+{
+    Shape s;
+    s.block_x = G.nx >= 1024 ? 128 : 64;
+    const int strips = (G.nx + s.block_x - 1) / s.block_x;
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int chunks = (2 * sms + strips - 1) / strips;
+    int rows = (G.ny + chunks - 1) / chunks;
+    if (rows < 8) rows = 8;
+    if (rows > 64) rows = 64;
+    s.rows = rows;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t tf_lbm_version(void) { return 100; }
+
+const char* tf_lbm_last_error(const tf_lbm_handle* H)
+{
+    return H ? H->err.c_str() : g_init_err.c_str();
+}
+
+int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0,
+                const void* theta, void* stream)
+{
+    g_init_err.clear();
+    if (!out) return fail(nullptr, TF_LBM_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    int rc = validate(params);
+    if (rc) return rc;
+    if ((rc = check_dev_ptr(nullptr, h0, "h0", false))) return rc;
+    if ((rc = check_dev_ptr(nullptr, theta, "theta", true))) return rc;
+
+    tf_lbm_handle* H = new tf_lbm_handle();
+    H->p = *params;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetDevice(&H->device);
+    H->esize = params->dtype == TF_LBM_F32 ? 4 : 8;
+    const int align = 128 / (int)H->esize;  // rows start on 128-byte boundaries
+    H->G.nx = params->nx;
+    H->G.ny = params->ny;
+    H->G.pitch = (params->nx + align - 1) / align * align;
+    H->G.plane = (long long)params->ny * H->G.pitch;
+    H->shape = default_shape(H->G);
+    H->graph_chunk = ((long long)params->nx * params->ny <= (1LL << 20)) ? 64 : 0;
+
+    auto bail = [&](int code) {
+        g_init_err = H->err;
+        tf_lbm_destroy(H);
+        return code;
+    };
+    const size_t bytes = 9ull * H->G.plane * H->esize;
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&H->buf[b], bytes)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc populations"));
+        if ((e = cudaMemsetAsync(H->buf[b], 0, bytes, st)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMemsetAsync"));
+    }
+    H->nmass = mass_blocks(H->G);
+    if ((e = cudaMalloc(&H->partials, sizeof(double) * 2 * H->nmass + sizeof(double))) != cudaSuccess)
+        return bail(cuda_fail(H, e, "cudaMalloc scratch"));
+    H->result = H->partials + 2 * H->nmass;
+    if ((e = cudaMalloc(&H->flag, sizeof(int))) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc flag"));
+
+    const double kscale = (double)(params->n_exp - 1) * (params->m_exp - 1) /
+                          ((double)(params->n_exp - params->m_exp) * params->hstar);
+    const long long n = (long long)params->nx * params->ny;
+    if (theta) {
+        if ((e = cudaMalloc(&H->kappa, n * H->esize)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc kappa"));
+        e = params->dtype == TF_LBM_F32
+                ? launch_kappa_f32((float*)H->kappa, (const float*)theta, params->nx, params->ny,
+                                   params->n_exp, params->m_exp, params->hstar, st)
+                : launch_kappa_f64((double*)H->kappa, (const double*)theta, params->nx, params->ny,
+                                   params->n_exp, params->m_exp, params->hstar, st);
+        if (e != cudaSuccess) return bail(cuda_fail(H, e, "kappa kernel"));
+    } else {
+        H->kappa_u = (1.0 - cos(params->theta_uniform)) * kscale;
+    }
+    e = params->dtype == TF_LBM_F32
+            ? launch_init_f32((float*)H->buf[0], (const float*)h0, H->G, (float)params->g, st)
+            : launch_init_f64((double*)H->buf[0], (const double*)h0, H->G, params->g, st);
+    if (e != cudaSuccess) return bail(cuda_fail(H, e, "init kernel"));
+    H->cur = 0;
+    *out = H;
+    return TF_LBM_OK;
+}
+
+int tf_lbm_step(tf_lbm_handle* H, int64_t nsteps, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(H, TF_LBM_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int chunk = H->graph_chunk;
+    while (nsteps > 0) {
+        if (chunk > 0 && nsteps >= chunk) {
+            cudaGraphExec_t& ex = H->exec[H->cur];
+            if (!ex) {
+                if (!H->cap) CK(H, cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+                CK(H, cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+                cudaError_t le = cudaSuccess;
+                for (int i = 0; i < chunk && le == cudaSuccess; ++i) le = launch_one_step(H, H->cur ^ (i & 1), H->cap);
+                cudaGraph_t g = nullptr;
+                cudaError_t ce = cudaStreamEndCapture(H->cap, &g);
+                if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(H, le, "step kernel (capture)"); }
+                if (ce != cudaSuccess) return cuda_fail(H, ce, "cudaStreamEndCapture");
+                cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) { ex = nullptr; return cuda_fail(H, ie, "cudaGraphInstantiate"); }
+            }
+            CK(H, cudaGraphLaunch(ex, st), "cudaGraphLaunch");
+            nsteps -= chunk;
+            H->time += chunk;
+        } else {
+            CK(H, launch_one_step(H, H->cur, st), "step kernel");
+            H->cur ^= 1;
+            --nsteps;
+            ++H->time;
+        }
+    }
+    return TF_LBM_OK;
+}
+
+int tf_lbm_moments(tf_lbm_handle* H, void* h, void* ux, void* uy, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(H, h, "h", true)) || (rc = check_dev_ptr(H, ux, "ux", true)) ||
+        (rc = check_dev_ptr(H, uy, "uy", true)))
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = H->p.dtype == TF_LBM_F32
+                        ? launch_moments_f32((const float*)H->buf[H->cur], (float*)h, (float*)ux, (float*)uy, H->G, st)
+                        : launch_moments_f64((const double*)H->buf[H->cur], (double*)h, (double*)ux, (double*)uy, H->G, st);
+    CK(H, e, "moments kernel");
+    return TF_LBM_OK;
+}
+
+int tf_lbm_pressure_force(tf_lbm_handle* H, void* p, void* fx, void* fy, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(H, p, "p", true)) || (rc = check_dev_ptr(H, fx, "fx", true)) ||
+        (rc = check_dev_ptr(H, fy, "fy", true)))
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = (long long)H->G.nx * H->G.ny;
+    if (!H->diag) CK(H, cudaMalloc(&H->diag, 2 * n * H->esize), "cudaMalloc diagnostics");
+    cudaError_t e;
+    if (H->p.dtype == TF_LBM_F32) {
+        float* s = (float*)H->diag;
+        e = launch_pressure_force_f32((const float*)H->buf[H->cur], (const float*)H->kappa, (float*)p,
+                                      (float*)fx, (float*)fy, s, s + n, H->G, make_consts<float>(H), st);
+    } else {
+        double* s = (double*)H->diag;
+        e = launch_pressure_force_f64((const double*)H->buf[H->cur], (const double*)H->kappa, (double*)p,
+                                      (double*)fx, (double*)fy, s, s + n, H->G, make_consts<double>(H), st);
+    }
+    CK(H, e, "pressure/force kernels");
+    return TF_LBM_OK;
+}
+
+int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    if (!mass_host) return fail(H, TF_LBM_ERR_ARG, "mass_host must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = H->p.dtype == TF_LBM_F32
+                        ? launch_mass_f32((const float*)H->buf[H->cur], H->G, H->partials, H->nmass, H->result, st)
+                        : launch_mass_f64((const double*)H->buf[H->cur], H->G, H->partials, H->nmass, H->result, st);
+    CK(H, e, "mass kernels");
+    CK(H, cudaMemcpyAsync(mass_host, H->result, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(H, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return TF_LBM_OK;
+}
+
+int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    if (!status_host) return fail(H, TF_LBM_ERR_ARG, "status_host must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(H, cudaMemsetAsync(H->flag, 0, sizeof(int), st), "cudaMemsetAsync");
+    cudaError_t e = H->p.dtype == TF_LBM_F32
+                        ? launch_check_f32((const float*)H->buf[H->cur], H->G, H->flag, st)
+                        : launch_check_f64((const double*)H->buf[H->cur], H->G, H->flag, st);
+    CK(H, e, "check kernel");
+    int v = 0;
+    CK(H, cudaMemcpyAsync(&v, H->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(H, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    *status_host = v;
+    return TF_LBM_OK;
+}
+
+int tf_lbm_get_state(tf_lbm_handle* H, void* f, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = H->p.dtype == TF_LBM_F32
+                        ? launch_get_state_f32((const float*)H->buf[H->cur], (float*)f, H->G, st)
+                        : launch_get_state_f64((const double*)H->buf[H->cur], (double*)f, H->G, st);
+    CK(H, e, "get_state kernel");
+    return TF_LBM_OK;
+}
+
+int tf_lbm_set_state(tf_lbm_handle* H, const void* f, void* stream)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = H->p.dtype == TF_LBM_F32
+                        ? launch_set_state_f32((float*)H->buf[H->cur], (const float*)f, H->G, st)
+                        : launch_set_state_f64((double*)H->buf[H->cur], (const double*)f, H->G, st);
+    CK(H, e, "set_state kernel");
+    return TF_LBM_OK;
+}
+
+int64_t tf_lbm_time(const tf_lbm_handle* H) { return H ? H->time : -1; }
+
+int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out)
+{
+    if (!H || !out) return TF_LBM_ERR_ARG;
+    out->block_x = H->shape.block_x;
+    out->rows = H->shape.rows;
+    out->graph_chunk = H->graph_chunk;
+    out->reserved = 0;
+    return TF_LBM_OK;
+}
+
+int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    if (!in) return fail(H, TF_LBM_ERR_ARG, "launch is NULL");
+    const int bx = in->block_x;
+    const bool ok_bx = H->p.dtype == TF_LBM_F32 ? (bx == 64 || bx == 128 || bx == 256) : (bx == 64 || bx == 128);
+    if (!ok_bx) return fail(H, TF_LBM_ERR_ARG, "block_x must be 64, 128 or 256 (64 or 128 for FP64)");
+    if (in->rows < 1 || in->rows > 65535) return fail(H, TF_LBM_ERR_ARG, "rows must be in [1, 65535]");
+    if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
+        return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
+    drop_graphs(H);
+    H->shape.block_x = bx;
+    H->shape.rows = in->rows;
+    H->graph_chunk = in->graph_chunk;
+    return TF_LBM_OK;
+}
+
+void tf_lbm_destroy(tf_lbm_handle* H)
+{
+    if (!H) return;
+    cudaDeviceSynchronize();
+    drop_graphs(H);
+    if (H->cap) cudaStreamDestroy(H->cap);
+    for (auto& b : H->buf)
+        if (b) cudaFree(b);
+    if (H->kappa) cudaFree(H->kappa);
+    if (H->partials) cudaFree(H->partials);
+    if (H->flag) cudaFree(H->flag);
+    if (H->diag) cudaFree(H->diag);
+    delete H;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+"""Torch-facing wrapper of libtflbm: one thin-film simulation on one GPU.
+
+PyTorch only provides device memory and streams here; every step of the method
+runs in the library's CUDA kernels (include/tflbm.h).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _lib as L
+
+_DT = {"f32": (L.TF_LBM_F32, torch.float32), "f64": (L.TF_LBM_F64, torch.float64)}
+
+
+def make_params(nx, ny, dtype="f32", tau=1.0, gamma=0.01, g=0.0, delta=1.0, hstar=0.07,
+                n_exp=3, m_exp=2, pi_sign=1, gx_body=0.0, gy_body=0.0, theta_uniform=0.0,
+                **_ignored) -> L.Params:
+    code = _DT[dtype][0]
+    return L.Params(int(nx), int(ny), code, int(n_exp), int(m_exp), int(pi_sign), float(tau),
+                    float(gamma), float(g), float(delta), float(hstar), float(gx_body),
+                    float(gy_body), float(theta_uniform))
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class ThinFilm:
+    """A periodic nx x ny thin-film simulation (Section II of the paper).
+
+    h0 and theta are (ny, nx) tensors (any device/dtype; copied to the GPU in
+    the run's dtype).  theta=None uses ``theta_uniform`` (radians) everywhere.
+    """
+
+    def __init__(self, params: dict, h0, theta=None, dtype: str = "f32", stream=None,
+                 device="cuda"):
+        if dtype not in _DT:
+            raise ValueError(f"dtype must be one of {list(_DT)}")
+        self.dtype_name = dtype
+        self.tdtype = _DT[dtype][1]
+        self.device = torch.device(device)
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.cparams = make_params(dtype=dtype, **params)
+        self.stream = stream
+        h0 = torch.as_tensor(h0).to(device=self.device, dtype=self.tdtype).contiguous()
+        if tuple(h0.shape) != (self.ny, self.nx):
+            raise ValueError(f"h0 must have shape {(self.ny, self.nx)}")
+        th = None
+        if theta is not None:
+            th = torch.as_tensor(theta).to(device=self.device, dtype=self.tdtype).contiguous()
+            if tuple(th.shape) != (self.ny, self.nx):
+                raise ValueError(f"theta must have shape {(self.ny, self.nx)}")
+        st = _stream_ptr(stream)
+        self.handle = L.tf_lbm_init(self.cparams, h0.data_ptr(),
+                                    th.data_ptr() if th is not None else None, st)
+        # keep inputs alive until the init kernels have consumed them
+        self._keep = (h0, th)
+        self._st = st
+
+    # -- stepping and outputs -------------------------------------------------
+    def step(self, nsteps: int = 1):
+        L.tf_lbm_step(self.handle, nsteps, self._st)
+
+    def _field(self):
+        return torch.empty((self.ny, self.nx), dtype=self.tdtype, device=self.device)
+
+    def moments(self, want=("h", "ux", "uy")):
+        out = {k: self._field() for k in want}
+        L.tf_lbm_moments(self.handle, *(out[k].data_ptr() if k in out else None
+                                        for k in ("h", "ux", "uy")), self._st)
+        return out
+
+    def h(self):
+        return self.moments(("h",))["h"]
+
+    def pressure_force(self):
+        out = {k: self._field() for k in ("p", "fx", "fy")}
+        L.tf_lbm_pressure_force(self.handle, out["p"].data_ptr(), out["fx"].data_ptr(),
+                                out["fy"].data_ptr(), self._st)
+        return out
+
+    def mass(self) -> float:
+        return L.tf_lbm_mass(self.handle, self._st)
+
+    def check(self) -> int:
+        return L.tf_lbm_check(self.handle, self._st)
+
+    def get_state(self):
+        f = torch.empty((9, self.ny, self.nx), dtype=self.tdtype, device=self.device)
+        L.tf_lbm_get_state(self.handle, f.data_ptr(), self._st)
+        return f
+
+    def set_state(self, f):
+        f = torch.as_tensor(f).to(device=self.device, dtype=self.tdtype).contiguous()
+        L.tf_lbm_set_state(self.handle, f.data_ptr(), self._st)
+        self._keep = (f,)
+
+    @property
+    def time(self) -> int:
+        return L.tf_lbm_time(self.handle)
+
+    @property
+    def launch(self):
+        l = L.tf_lbm_get_launch(self.handle)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk)
+
+    def set_launch(self, block_x=None, rows=None, graph_chunk=None):
+        cur = self.launch
+        L.tf_lbm_set_launch(self.handle, block_x or cur["block_x"], rows or cur["rows"],
+                            cur["graph_chunk"] if graph_chunk is None else graph_chunk)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.tf_lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def theta_radians(deg) -> float:
+    return math.radians(deg)

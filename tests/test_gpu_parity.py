@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (relative L-infinity on h, max|h_gpu - h_oracle| / max|h_oracle|):
+  FP32 storage and arithmetic: 1e-5 after 1000 steps; relative mass drift 1e-6.
+  FP64: 1e-11 (only summation order and fused multiply-adds differ).
+The FP32 bound comes from the arithmetic: every step rounds each population
+to 2^-24 relative; the film dynamics are diffusive (friction-dominated), so
+per-step errors of ~1e-7 do not amplify and accumulate at most like a random
+walk, ~sqrt(1000) x 1e-7 = 3e-6 after 1000 steps.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1810_07642_gb300 import inputs
+from paper_1810_07642_gb300 import _lib as L
+from paper_1810_07642_gb300.film import ThinFilm
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "f64": 1e-11}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    from paper_1810_07642_gb300 import build
+    build.build()
+    O.set_num_threads(os.cpu_count() or 1)
+    assert torch.cuda.is_available()
+    yield
+
+
+def cfg_of(p, **over):
+    d = {k: v for k, v in p.items() if k in O.Config.__dataclass_fields__}
+    d.update(over)
+    return O.Config(**d)
+
+
+def rel_linf(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def run_both(h0, theta, p, steps, dtype="f32", launch=None, theta_uniform=None):
+    cfg = cfg_of(p)
+    th_o = theta if theta_uniform is None else theta_uniform
+    kap = O.kappa_field(cfg, th_o)
+    f = O.init(cfg, h0)
+    m0 = O.mass(cfg, f)
+    O.step(cfg, kap, f, steps)
+    ho, uxo, uyo = O.moments(cfg, f)
+    pp = dict(p)
+    if theta_uniform is not None:
+        pp["theta_uniform"] = theta_uniform
+    sim = ThinFilm(pp, h0, None if theta_uniform is not None else theta, dtype=dtype)
+    if launch:
+        sim.set_launch(**launch)
+    gm0 = sim.mass()
+    sim.step(steps)
+    mom = sim.moments()
+    gm1 = sim.mass()
+    torch.cuda.synchronize()
+    out = {k: v.double().cpu().numpy() for k, v in mom.items()}
+    sim.close()
+    return dict(ho=ho, uxo=uxo, uyo=uyo, mo=m0, h=out["h"], ux=out["ux"], uy=out["uy"],
+                gm0=gm0, gm1=gm1)
+
+
+# ------------------------------------------------------------ small cases
+
+SMALL = [(37, 29), (130, 70), (200, 33), (64, 64), (5, 7), (3, 3), (1, 1), (2, 9)]
+
+
+@pytest.mark.parametrize("nx,ny", SMALL)
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_parity_random_film_patterned(nx, ny, dtype):
+    h0, th, p = inputs.small_random(nx, ny, seed=nx * 1000 + ny, amp=0.05)
+    p.update(tau=0.9, g=2e-4, gx_body=2e-5, gy_body=-1e-5, delta=1.0)
+    r = run_both(h0, th, p, 100, dtype)
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+    scale = max(np.abs(r["uxo"]).max(), np.abs(r["uyo"]).max(), 1e-12)
+    assert np.abs(r["ux"] - r["uxo"]).max() <= 1e2 * TOL[dtype] * scale + 1e-12
+    assert np.abs(r["uy"] - r["uyo"]).max() <= 1e2 * TOL[dtype] * scale + 1e-12
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.7, 1.6])
+def test_parity_uniform_theta_tau(tau):
+    h0, th, p = inputs.small_random(96, 80, seed=3, amp=0.1)
+    p.update(tau=tau, delta=0.5)
+    r = run_both(h0, th, p, 200, "f32", theta_uniform=math.radians(25))
+    assert rel_linf(r["h"], r["ho"]) <= TOL["f32"]
+
+
+def test_parity_rayleigh_taylor_128_fp32_and_fp64():
+    """128 x 128 hanging film (g = -1e-4, delta = 0, kappa = 0), 1000 steps."""
+    h0, th, p = inputs.rayleigh_taylor(128)
+    for dtype in ("f32", "f64"):
+        r = run_both(h0, th, p, 1000, dtype)
+        assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+        # the perturbation itself (h - 1 ~ 1e-3) must match too
+        dh, dho = r["h"] - 1.0, r["ho"] - 1.0
+        assert np.abs(dh - dho).max() <= (1e-3 if dtype == "f32" else 1e-9) * np.abs(dho).max()
+        assert abs(r["gm1"] - r["mo"]) <= 1e-6 * r["mo"]
+
+
+def test_parity_sessile_drop_256_fp32():
+    """Spherical-cap drop on a precursor film (theta = 20 deg, delta = 1)."""
+    h0, th, p = inputs.sessile_drop(256, rb=60.0, hd=10.0)
+    r = run_both(h0, th, p, 1000, "f32", theta_uniform=math.radians(20))
+    assert rel_linf(r["h"], r["ho"]) <= TOL["f32"]
+    assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
+    assert abs(r["gm0"] - r["mo"]) <= 1e-6 * r["mo"]
+
+
+def test_parity_patterned_dewetting_256_fp32():
+    h0, th, p = inputs.patterned_dewetting(256, seed=1)
+    r = run_both(h0, th, p, 1000, "f32")
+    assert rel_linf(r["h"], r["ho"]) <= TOL["f32"]
+    assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
+
+
+@pytest.mark.parametrize("shape", [dict(block_x=64, rows=1), dict(block_x=64, rows=5),
+                                   dict(block_x=128, rows=64), dict(block_x=256, rows=17),
+                                   dict(block_x=128, rows=3, graph_chunk=4)])
+def test_launch_shape_does_not_change_results(shape):
+    """Every node does the same arithmetic in the same order whatever the CTA
+    shape or graph chunking, so results are bitwise identical."""
+    h0, th, p = inputs.small_random(300, 141, seed=9, amp=0.05)
+    ref = ThinFilm(p, h0, th)
+    ref.set_launch(block_x=64, rows=64, graph_chunk=0)
+    ref.step(23)
+    other = ThinFilm(p, h0, th)
+    other.set_launch(**shape)
+    other.step(23)
+    a, b = ref.get_state(), other.get_state()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+# ------------------------------------------------------- full-size sampled
+
+def _window(f, y, x, rad):
+    ny, nx = f.shape[1:]
+    ys = (np.arange(y - rad, y + rad + 1)) % ny
+    xs = (np.arange(x - rad, x + rad + 1)) % nx
+    return np.ascontiguousarray(f[:, ys][:, :, xs])
+
+
+def test_full_size_patterned_2048_sampled_against_oracle():
+    """2048 x 2048 patterned dewetting in the default launch shape.  After k
+    steps the population at a node depends only on the state within radius 3k
+    (pull: radius 1, grad p: +1, lap h: +1, h: +1), so the oracle can advance
+    a (6k+1)^2 window cut from the GPU state and compare its centre."""
+    h0, th, p = inputs.patterned_dewetting(2048, seed=0)
+    sim = ThinFilm(p, h0, th)
+    sim.step(50)  # develop some dynamics first
+    f0 = sim.get_state().double().cpu().numpy()
+    k = 3
+    sim.step(k)
+    f1 = sim.get_state().double().cpu().numpy()
+    assert sim.check() == 0
+    sim.close()
+    rng = np.random.default_rng(0)
+    bx = 128
+    pts = [(0, 0), (2047, 2047), (0, 2047), (2047, 0), (63, bx - 1), (64, bx), (1000, 1023)]
+    pts += [(int(y), int(x)) for y, x in zip(rng.integers(0, 2048, 57), rng.integers(0, 2048, 57))]
+    rad = 3 * k
+    worst = 0.0
+    cfg = cfg_of(p, nx=2 * rad + 1, ny=2 * rad + 1)
+    for (y, x) in pts:
+        fw = _window(f0, y, x, rad)
+        thw = th[(np.arange(y - rad, y + rad + 1) % 2048)][:, (np.arange(x - rad, x + rad + 1) % 2048)]
+        O.step(cfg, O.kappa_field(cfg, thw), fw, k)
+        got = f1[:, y, x]
+        worst = max(worst, np.abs(fw[:, rad, rad] - got).max() / np.abs(fw[:, rad, rad]).max())
+    assert worst <= 1e-5, worst
+
+
+def test_full_size_mass_conservation_and_check():
+    h0, th, p = inputs.patterned_dewetting(2048, seed=2)
+    sim = ThinFilm(p, h0, th)
+    m0 = sim.mass()
+    ref = float(np.asarray(h0, np.float32).astype(np.float64).sum())
+    assert abs(m0 - ref) <= 1e-6 * ref
+    sim.step(300)
+    m1 = sim.mass()
+    assert abs(m1 - m0) <= 1e-6 * m0
+    assert sim.check() == 0
+    sim.close()
+
+
+# ------------------------------------------------------------ API behaviour
+
+def test_initial_moments_are_h0_at_rest():
+    h0, th, p = inputs.small_random(50, 40, seed=4, amp=0.2)
+    sim = ThinFilm(p, h0, th, dtype="f64")
+    m = sim.moments()
+    assert torch.allclose(m["h"].cpu(), torch.as_tensor(h0), rtol=1e-15, atol=0)
+    assert m["ux"].abs().max().item() < 1e-15 and m["uy"].abs().max().item() < 1e-15
+    assert sim.time == 0
+
+
+def test_flat_film_stays_flat_on_gpu():
+    p = inputs._params(70, 50, g=-1e-4, tau=0.8)
+    p["theta_uniform"] = 0.3
+    sim = ThinFilm(p, np.full((50, 70), 1.3), None)
+    sim.step(100)
+    m = sim.moments()
+    assert (m["h"].max() - m["h"].min()).item() == 0.0
+    assert m["ux"].abs().max().item() == 0.0 and m["uy"].abs().max().item() == 0.0
+
+
+def test_pressure_force_diagnostic_matches_oracle():
+    h0, th, p = inputs.small_random(64, 48, seed=6, amp=0.1)
+    p.update(gx_body=1e-5, delta=0.3)
+    cfg = cfg_of(p)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    O.step(cfg, kap, f, 20)
+    po, fxo, fyo = O.pressure_force(cfg, kap, f)
+    sim = ThinFilm(p, h0, th, dtype="f64")
+    sim.step(20)
+    d = {k: v.cpu().numpy() for k, v in sim.pressure_force().items()}
+    assert rel_linf(d["p"], po) < 1e-10
+    assert np.abs(d["fx"] - fxo).max() < 1e-10 * np.abs(fxo).max()
+    assert np.abs(d["fy"] - fyo).max() < 1e-10 * np.abs(fyo).max()
+
+
+def test_state_roundtrip_resumes_bitwise():
+    h0, th, p = inputs.small_random(90, 70, seed=8, amp=0.1)
+    a = ThinFilm(p, h0, th)
+    a.step(17)
+    s = a.get_state()
+    b = ThinFilm(p, h0, th)
+    b.set_state(s)
+    a.step(9)
+    b.step(9)
+    assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_invalid_arguments_are_rejected():
+    h0 = torch.ones((8, 8), device="cuda")
+    base = dict(inputs._params(8, 8))
+    for bad in (dict(tau=0.5), dict(hstar=0.0), dict(n_exp=2, m_exp=2), dict(pi_sign=0),
+                dict(delta=-1.0), dict(nx=0)):
+        q = dict(base, **bad)
+        with pytest.raises(L.TfLbmError) as e:
+            ThinFilm(q, torch.ones((max(q["ny"], 1), max(q["nx"], 1)), device="cuda"))
+        assert e.value.code == L.TF_LBM_ERR_ARG
+    prm = __import__("paper_1810_07642_gb300.film", fromlist=["make_params"]).make_params(8, 8)
+    hh = np.ones((8, 8), np.float32)
+    with pytest.raises(L.TfLbmError) as e:
+        L.tf_lbm_init(prm, hh.ctypes.data, None, 0)  # host pointer
+    assert e.value.code == L.TF_LBM_ERR_ARG and "device" in str(e.value)
+    sim = ThinFilm(base, h0)
+    with pytest.raises(L.TfLbmError):
+        sim.step(-1)
+    with pytest.raises(L.TfLbmError):
+        sim.set_launch(block_x=96)
+    with pytest.raises(L.TfLbmError):
+        sim.set_launch(graph_chunk=3)
+
+
+def test_check_reports_nonfinite_and_nonpositive():
+    p = inputs._params(16, 16)
+    h0 = np.ones((16, 16))
+    h0[3, 4] = np.nan
+    assert ThinFilm(p, h0).check() & L.TF_LBM_STATUS_NONFINITE
+    h0 = np.ones((16, 16))
+    h0[5, 5] = 0.0
+    assert ThinFilm(p, h0).check() & L.TF_LBM_STATUS_NONPOSITIVE
+    assert ThinFilm(p, np.ones((16, 16))).check() == 0
+
+
+def test_no_slip_precursor_diverges_and_is_reported():
+    """With delta = 0 the explicit friction factor 1 - nu alpha / h is about
+    -100 on the h* = 0.07 precursor, so the sessile-drop run diverges; the
+    library must report it rather than hide it."""
+    h0, th, p = inputs.sessile_drop(128, rb=30.0, hd=5.0, delta=0.0)
+    p["theta_uniform"] = math.radians(20)
+    sim = ThinFilm(p, h0, None)
+    status = 0
+    for _ in range(50):
+        sim.step(20)
+        status = sim.check()
+        if status:
+            break
+    assert status & (L.TF_LBM_STATUS_NONFINITE | L.TF_LBM_STATUS_NONPOSITIVE)
