@@ -72,6 +72,21 @@ def profiled_traffic():
     return float(d["dram_bytes_per_launch"]), d
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job MLUPS: every rank advanced its own replica of `nodes` nodes."""
+    return world * nodes * steps / t_max / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -247,14 +262,10 @@ def run_tflbm(args):
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     t_local = total_ms / 1e3
-    t_max = t_local
-    if dist:
-        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_local, dist, "cuda")
     m1 = sim.mass()
     status = sim.check()
-    value = world * nodes * args.steps / t_max / 1e6
+    value = aggregate_mlups(nodes, args.steps, world, t_max)
 
     # dominant kernel: the fused step, one launch per step
     kern_s = statistics.fmean(per) / 1e3
@@ -278,13 +289,9 @@ def run_tflbm(args):
         hres = sim2.moments(("h",))["h"]
         out_host.copy_(hres, non_blocking=True)
     stream.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     sim2.close()
-    e2e = {"value": world * nodes * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+    e2e = {"value": aggregate_mlups(nodes, args.steps, world, t_e2e), "unit": "MLUPS",
            "h2d_bytes_per_step": (h_host.numel() + th_host.numel()) * 4 / args.steps,
            "d2h_bytes_per_step": out_host.numel() * 4 / args.steps,
            "job": f"upload h0+theta, init, {args.steps} steps, download h (host wall clock)"}

@@ -139,7 +139,10 @@ int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream);
 int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream);
 
 /* Copy the post-streaming populations f_l(x, t) out to / in from a device
- * [9][ny][nx] buffer of the handle's dtype (checkpoint / resume). */
+ * [9][ny][nx] buffer of DOUBLES, whatever the handle's dtype (checkpoint /
+ * resume).  For TF_LBM_F32 the export is exact and importing an exported
+ * state reproduces the stored values bit for bit; other imported values are
+ * rounded to float. */
 int tf_lbm_get_state(tf_lbm_handle* H, void* f, void* stream);
 int tf_lbm_set_state(tf_lbm_handle* H, const void* f, void* stream);
 

@@ -14,4 +14,14 @@ cudaError_t launch_step_f32(const float* fin, float* fout, const float* kappa, c
     }
 }
 
+int step_blocks_per_sm_f32(int block_x, bool omega1, bool kfield)
+{
+    switch (block_x) {
+        case 64: return blocks_per_sm_bx<float, float, 64>(omega1, kfield);
+        case 128: return blocks_per_sm_bx<float, float, 128>(omega1, kfield);
+        case 256: return blocks_per_sm_bx<float, float, 256>(omega1, kfield);
+        default: return 0;
+    }
+}
+
 }  // namespace tflbm

@@ -13,4 +13,13 @@ cudaError_t launch_step_f64(const double* fin, double* fout, const double* kappa
     }
 }
 
+int step_blocks_per_sm_f64(int block_x, bool omega1, bool kfield)
+{
+    switch (block_x) {
+        case 64: return blocks_per_sm_bx<double, double, 64>(omega1, kfield);
+        case 128: return blocks_per_sm_bx<double, double, 128>(omega1, kfield);
+        default: return 0;
+    }
+}
+
 }  // namespace tflbm

@@ -23,6 +23,7 @@ struct tf_lbm_handle {
     int cur = 0;               // buf[cur] holds the post-collision populations of step t-1
     void* kappa = nullptr;     // [ny][nx] or null (uniform)
     double kappa_u = 0.0;
+    double href = 0.0;         // reference height (exactly representable in the storage type)
     double* partials = nullptr;
     double* result = nullptr;
     int nmass = 0;
@@ -96,6 +97,7 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.gy = T(H->p.gy_body);
     C.kappa_u = T(H->kappa_u);
     C.pi_sgn = T(H->p.pi_sign);
+    C.href = T(H->href);
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
     return C;
@@ -146,19 +148,28 @@ int validate(const tf_lbm_params* p)
     return TF_LBM_OK;
 }
 
-Shape default_shape(const Geom& G)
+// Default launch shape: 128-wide CTAs on wide lattices, 64 otherwise, and a
+// band height that makes the grid one full wave of resident CTAs (all bands
+// do the same work, so a partial second wave would idle most SMs), but no
+// shorter than 16 rows: each band spends 5 warm-up rows.
+Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 {
     Shape s;
     s.block_x = G.nx >= 1024 ? 128 : 64;
-    const int strips = (G.nx + s.block_x - 1) / s.block_x;
+    const int strips = (G.nx + s.block_x - 5) / (s.block_x - 4);  // CTAs overlap by 4 columns
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int chunks = (2 * sms + strips - 1) / strips;
-    int rows = (G.ny + chunks - 1) / chunks;
-    if (rows < 8) rows = 8;
-    if (rows > 64) rows = 64;
+    const bool om1 = p.tau == 1.0;
+    int occ = p.dtype == TF_LBM_F32 ? step_blocks_per_sm_f32(s.block_x, om1, kfield)
+                                    : step_blocks_per_sm_f64(s.block_x, om1, kfield);
+    if (occ < 1) occ = 4;
+    int bands = occ * sms / strips;
+    if (bands < 1) bands = 1;
+    int rows = (G.ny + bands - 1) / bands;
+    if (rows < 16) rows = 16;
+    if (rows > 4096) rows = 4096;
     s.rows = rows;
     return s;
 }
@@ -195,7 +206,12 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     H->G.ny = params->ny;
     H->G.pitch = (params->nx + align - 1) / align * align;
     H->G.plane = (long long)params->ny * H->G.pitch;
-    H->shape = default_shape(H->G);
+    if (9LL * H->G.plane >= (1LL << 31)) {
+        delete H;
+        return fail(nullptr, TF_LBM_ERR_UNSUPPORTED,
+                    "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
+    }
+    H->shape = default_shape(*params, H->G, theta != nullptr);
     H->graph_chunk = ((long long)params->nx * params->ny <= (1LL << 20)) ? 64 : 0;
 
     auto bail = [&](int code) {
@@ -210,6 +226,7 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
         if ((e = cudaMemsetAsync(H->buf[b], 0, bytes, st)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMemsetAsync"));
     }
     H->nmass = mass_blocks(H->G);
+    if (H->nmass < kSumBlocks) H->nmass = kSumBlocks;
     if ((e = cudaMalloc(&H->partials, sizeof(double) * 2 * H->nmass + sizeof(double))) != cudaSuccess)
         return bail(cuda_fail(H, e, "cudaMalloc scratch"));
     H->result = H->partials + 2 * H->nmass;
@@ -229,9 +246,21 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     } else {
         H->kappa_u = (1.0 - cos(params->theta_uniform)) * kscale;
     }
+    // reference height: the mean of h0, rounded to the storage type
     e = params->dtype == TF_LBM_F32
-            ? launch_init_f32((float*)H->buf[0], (const float*)h0, H->G, (float)params->g, st)
-            : launch_init_f64((double*)H->buf[0], (const double*)h0, H->G, params->g, st);
+            ? launch_sum_f32((const float*)h0, n, H->partials, H->nmass, H->result, st)
+            : launch_sum_f64((const double*)h0, n, H->partials, H->nmass, H->result, st);
+    if (e != cudaSuccess) return bail(cuda_fail(H, e, "sum kernel"));
+    double hsum = 0.0;
+    if ((e = cudaMemcpyAsync(&hsum, H->result, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return bail(cuda_fail(H, e, "reading the mean height"));
+    const double mean = hsum / (double)n;
+    H->href = params->dtype == TF_LBM_F32 ? (double)(float)mean : mean;
+    if (!isfinite(H->href)) H->href = 0.0;  // a non-finite h0 is reported by tf_lbm_check
+    e = params->dtype == TF_LBM_F32
+            ? launch_init_f32((float*)H->buf[0], (const float*)h0, H->G, (float)params->g, (float)H->href, st)
+            : launch_init_f64((double*)H->buf[0], (const double*)h0, H->G, params->g, H->href, st);
     if (e != cudaSuccess) return bail(cuda_fail(H, e, "init kernel"));
     H->cur = 0;
     *out = H;
@@ -282,8 +311,10 @@ int tf_lbm_moments(tf_lbm_handle* H, void* h, void* ux, void* uy, void* stream)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_moments_f32((const float*)H->buf[H->cur], (float*)h, (float*)ux, (float*)uy, H->G, st)
-                        : launch_moments_f64((const double*)H->buf[H->cur], (double*)h, (double*)ux, (double*)uy, H->G, st);
+                        ? launch_moments_f32((const float*)H->buf[H->cur], (float*)h, (float*)ux, (float*)uy, H->G,
+                                             (float)H->href, st)
+                        : launch_moments_f64((const double*)H->buf[H->cur], (double*)h, (double*)ux, (double*)uy, H->G,
+                                             H->href, st);
     CK(H, e, "moments kernel");
     return TF_LBM_OK;
 }
@@ -323,6 +354,8 @@ int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream)
     CK(H, e, "mass kernels");
     CK(H, cudaMemcpyAsync(mass_host, H->result, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     CK(H, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    // plane 0 stores f_0 - href: add href back once per node
+    *mass_host += H->href * (double)H->G.nx * (double)H->G.ny;
     return TF_LBM_OK;
 }
 
@@ -333,8 +366,8 @@ int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     CK(H, cudaMemsetAsync(H->flag, 0, sizeof(int), st), "cudaMemsetAsync");
     cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_check_f32((const float*)H->buf[H->cur], H->G, H->flag, st)
-                        : launch_check_f64((const double*)H->buf[H->cur], H->G, H->flag, st);
+                        ? launch_check_f32((const float*)H->buf[H->cur], H->G, (float)H->href, H->flag, st)
+                        : launch_check_f64((const double*)H->buf[H->cur], H->G, H->href, H->flag, st);
     CK(H, e, "check kernel");
     int v = 0;
     CK(H, cudaMemcpyAsync(&v, H->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
@@ -350,8 +383,8 @@ int tf_lbm_get_state(tf_lbm_handle* H, void* f, void* stream)
     if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_get_state_f32((const float*)H->buf[H->cur], (float*)f, H->G, st)
-                        : launch_get_state_f64((const double*)H->buf[H->cur], (double*)f, H->G, st);
+                        ? launch_get_state_f32((const float*)H->buf[H->cur], (double*)f, H->G, (float)H->href, st)
+                        : launch_get_state_f64((const double*)H->buf[H->cur], (double*)f, H->G, H->href, st);
     CK(H, e, "get_state kernel");
     return TF_LBM_OK;
 }
@@ -363,8 +396,8 @@ int tf_lbm_set_state(tf_lbm_handle* H, const void* f, void* stream)
     if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_set_state_f32((float*)H->buf[H->cur], (const float*)f, H->G, st)
-                        : launch_set_state_f64((double*)H->buf[H->cur], (const double*)f, H->G, st);
+                        ? launch_set_state_f32((float*)H->buf[H->cur], (const double*)f, H->G, (float)H->href, st)
+                        : launch_set_state_f64((double*)H->buf[H->cur], (const double*)f, H->G, H->href, st);
     CK(H, e, "set_state kernel");
     return TF_LBM_OK;
 }

@@ -2,7 +2,8 @@
 // populations, moments, film pressure and force (diagnostic), compensated
 // mass, state scan and state import/export.  The stored buffer holds
 // post-collision (pre-streaming) populations B_l, so the post-streaming
-// populations of the current time are f_l(x) = B_l(x - c_l).
+// populations of the current time are f_l(x) = B_l(x - c_l); plane 0 stores
+// B_0 - href (the reference height convention of tflbm_internal.h).
 #include <math.h>
 
 #include "tflbm_internal.h"
@@ -19,14 +20,17 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i < 0 ? i + n : i;
 }
 
+// Post-streaming populations at (x, y), with the rest population restored.
 template <typename T>
-__device__ __forceinline__ void pull_at(const T* __restrict__ f, const Geom& G, int x, int y, T (&v)[9])
+__device__ __forceinline__ void pull_at(const T* __restrict__ f, const Geom& G, int x, int y,
+                                        T href, T (&v)[9])
 {
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
         const int xs = wrapi(x - kCx[l], G.nx), ys = wrapi(y - kCy[l], G.ny);
         v[l] = f[l * G.plane + (long long)ys * G.pitch + xs];
     }
+    v[0] += href;
 }
 
 template <typename T>
@@ -49,7 +53,7 @@ __global__ void k_kappa(T* kappa, const T* theta, long long n, int ne, int me, d
 
 // B_l(x) = f_eq_l(h0(x + c_l), u = 0), so that the pull gives f = f_eq(h0, 0).
 template <typename T>
-__global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g)
+__global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g, T href)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -59,7 +63,7 @@ __global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g)
         const T h = h0[(long long)wrapi(y + kCy[l], G.ny) * G.nx + wrapi(x + kCx[l], G.nx)];
         const T gh2 = g * h * h;
         T v;
-        if (l == 0) v = h - T(5.0 / 6.0) * gh2;
+        if (l == 0) v = (h - href) - T(5.0 / 6.0) * gh2;
         else if (l & 1) v = gh2 * T(1.0 / 6.0);
         else v = gh2 * T(1.0 / 24.0);
         f[l * G.plane + (long long)y * G.pitch + x] = v;
@@ -67,13 +71,13 @@ __global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g)
 }
 
 template <typename T>
-__global__ void k_moments(const T* __restrict__ f, T* h, T* ux, T* uy, Geom G)
+__global__ void k_moments(const T* __restrict__ f, T* h, T* ux, T* uy, Geom G, T href)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, v);
+    pull_at(f, G, x, y, href, v);
     moments9(v, hh, jx, jy);
     const long long i = (long long)y * G.nx + x;
     if (h) h[i] = hh;
@@ -83,13 +87,13 @@ __global__ void k_moments(const T* __restrict__ f, T* h, T* ux, T* uy, Geom G)
 
 // Diagnostic film pressure and force, in three plain passes.
 template <typename T>
-__global__ void k_pf_h(const T* __restrict__ f, T* hbuf, Geom G)
+__global__ void k_pf_h(const T* __restrict__ f, T* hbuf, Geom G, Consts<T> C)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, v);
+    pull_at(f, G, x, y, C.href, v);
     moments9(v, hh, jx, jy);
     hbuf[(long long)y * G.nx + x] = hh;
 }
@@ -135,7 +139,7 @@ __global__ void k_pf_f(const T* __restrict__ f, const T* __restrict__ pbuf, T* p
     const T gpx = (P(y, xp) - P(y, xm)) / T(3) + (P(yp, xp) - P(yp, xm) + P(ym, xp) - P(ym, xm)) / T(12);
     const T gpy = (P(yp, x) - P(ym, x)) / T(3) + (P(yp, xp) - P(ym, xp) + P(yp, xm) - P(ym, xm)) / T(12);
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, v);
+    pull_at(f, G, x, y, C.href, v);
     moments9(v, hh, jx, jy);
     const T fr = C.nu6 / (T(2) * hh * hh + T(6) * C.delta * hh + T(3) * C.delta * C.delta);
     const long long i = (long long)y * G.nx + x;
@@ -204,6 +208,30 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(const T* __restri
     }
 }
 
+// Plain compensated sum of n values (used for the mean initial height).
+template <typename T>
+__global__ void __launch_bounds__(kMassThreads) k_sum_partial(const T* __restrict__ x, long long n,
+                                                              double* partials)
+{
+    Comp a{0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        comp_add(a, (double)x[i]);
+    a = warp_reduce(a);
+    __shared__ Comp sm[kMassThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = a;
+    __syncthreads();
+    if (wid == 0) {
+        Comp b = lane < kMassThreads / 32 ? sm[lane] : Comp{0.0, 0.0};
+        b = warp_reduce(b);
+        if (lane == 0) {
+            partials[2 * blockIdx.x] = b.s;
+            partials[2 * blockIdx.x + 1] = b.c;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* partials, int n, double* out)
 {
     Comp a{0.0, 0.0};
@@ -224,14 +252,14 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* parti
 }
 
 template <typename T>
-__global__ void k_check(const T* __restrict__ f, Geom G, int* flag)
+__global__ void k_check(const T* __restrict__ f, Geom G, T href, int* flag)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     int bad = 0;
     if (x < G.nx) {
         T v[9], hh, jx, jy;
-        pull_at(f, G, x, y, v);
+        pull_at(f, G, x, y, href, v);
         for (int l = 0; l < 9; ++l)
             if (!isfinite((double)v[l])) bad |= 1;
         moments9(v, hh, jx, jy);
@@ -242,21 +270,25 @@ __global__ void k_check(const T* __restrict__ f, Geom G, int* flag)
     if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, bad);
 }
 
+// State export in double: (f_0 - href) + href is exact in double for float
+// storage, so an export / import round trip reproduces the stored bits.
 template <typename T>
-__global__ void k_get_state(const T* __restrict__ f, T* out, Geom G)
+__global__ void k_get_state(const T* __restrict__ f, double* out, Geom G, T href)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
-    T v[9];
-    pull_at(f, G, x, y, v);
     const long long n = (long long)G.nx * G.ny, i = (long long)y * G.nx + x;
 #pragma unroll
-    for (int l = 0; l < 9; ++l) out[l * n + i] = v[l];
+    for (int l = 0; l < 9; ++l) {
+        const int xs = wrapi(x - kCx[l], G.nx), ys = wrapi(y - kCy[l], G.ny);
+        const double v = (double)f[l * G.plane + (long long)ys * G.pitch + xs];
+        out[l * n + i] = l == 0 ? v + (double)href : v;
+    }
 }
 
 template <typename T>
-__global__ void k_set_state(T* f, const T* __restrict__ in, Geom G)
+__global__ void k_set_state(T* f, const double* __restrict__ in, Geom G, T href)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -265,7 +297,8 @@ __global__ void k_set_state(T* f, const T* __restrict__ in, Geom G)
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
         const long long src = (long long)wrapi(y + kCy[l], G.ny) * G.nx + wrapi(x + kCx[l], G.nx);
-        f[l * G.plane + (long long)y * G.pitch + x] = in[l * n + src];
+        const double v = in[l * n + src];
+        f[l * G.plane + (long long)y * G.pitch + x] = T(l == 0 ? v - (double)href : v);
     }
 }
 
@@ -288,22 +321,30 @@ int mass_blocks(const Geom& G)
         k_kappa<T><<<blocks, 256, 0, st>>>(kappa, theta, n, ne, me, hstar);                     \
         return cudaGetLastError();                                                              \
     }                                                                                           \
-    cudaError_t launch_init_##SUF(T* f, const T* h0, const Geom& G, T g, cudaStream_t st)      \
+    cudaError_t launch_init_##SUF(T* f, const T* h0, const Geom& G, T g, T href,              \
+                                  cudaStream_t st)                                             \
     {                                                                                           \
-        k_init<T><<<grid2d(G, 128), 128, 0, st>>>(f, h0, G, g);                                 \
+        k_init<T><<<grid2d(G, 128), 128, 0, st>>>(f, h0, G, g, href);                           \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_moments_##SUF(const T* f, T* h, T* ux, T* uy, const Geom& G,             \
-                                     cudaStream_t st)                                          \
+                                     T href, cudaStream_t st)                                  \
     {                                                                                           \
-        k_moments<T><<<grid2d(G, 128), 128, 0, st>>>(f, h, ux, uy, G);                          \
+        k_moments<T><<<grid2d(G, 128), 128, 0, st>>>(f, h, ux, uy, G, href);                    \
+        return cudaGetLastError();                                                              \
+    }                                                                                           \
+    cudaError_t launch_sum_##SUF(const T* x, long long n, double* partials, int nblocks,        \
+                                 double* result, cudaStream_t st)                              \
+    {                                                                                           \
+        k_sum_partial<T><<<nblocks, kMassThreads, 0, st>>>(x, n, partials);                     \
+        k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);                    \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_pressure_force_##SUF(const T* f, const T* kappa, T* p, T* fx, T* fy,     \
                                             T* sh, T* sp, const Geom& G, const Consts<T>& C,    \
                                             cudaStream_t st)                                   \
     {                                                                                           \
-        k_pf_h<T><<<grid2d(G, 128), 128, 0, st>>>(f, sh, G);                                    \
+        k_pf_h<T><<<grid2d(G, 128), 128, 0, st>>>(f, sh, G, C);                                 \
         k_pf_p<T><<<grid2d(G, 128), 128, 0, st>>>(sh, kappa, sp, G, C);                         \
         k_pf_f<T><<<grid2d(G, 128), 128, 0, st>>>(f, sp, p, fx, fy, G, C);                      \
         return cudaGetLastError();                                                              \
@@ -315,19 +356,22 @@ int mass_blocks(const Geom& G)
         k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);                    \
         return cudaGetLastError();                                                              \
     }                                                                                           \
-    cudaError_t launch_check_##SUF(const T* f, const Geom& G, int* flag, cudaStream_t st)      \
+    cudaError_t launch_check_##SUF(const T* f, const Geom& G, T href, int* flag,               \
+                                   cudaStream_t st)                                            \
     {                                                                                           \
-        k_check<T><<<grid2d(G, 128), 128, 0, st>>>(f, G, flag);                                 \
+        k_check<T><<<grid2d(G, 128), 128, 0, st>>>(f, G, href, flag);                           \
         return cudaGetLastError();                                                              \
     }                                                                                           \
-    cudaError_t launch_get_state_##SUF(const T* f, T* out, const Geom& G, cudaStream_t st)     \
+    cudaError_t launch_get_state_##SUF(const T* f, double* out, const Geom& G, T href,         \
+                                       cudaStream_t st)                                        \
     {                                                                                           \
-        k_get_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, out, G);                              \
+        k_get_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, out, G, href);                        \
         return cudaGetLastError();                                                              \
     }                                                                                           \
-    cudaError_t launch_set_state_##SUF(T* f, const T* in, const Geom& G, cudaStream_t st)      \
+    cudaError_t launch_set_state_##SUF(T* f, const double* in, const Geom& G, T href,          \
+                                       cudaStream_t st)                                        \
     {                                                                                           \
-        k_set_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, in, G);                               \
+        k_set_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, in, G, href);                         \
         return cudaGetLastError();                                                              \
     }
 

@@ -8,17 +8,25 @@
 //  * Populations live in SoA planes [9][ny][pitch].  The buffer read by a step
 //    holds post-collision values of the previous step, so streaming is a pull:
 //    f_l(x, y) = fin_l(x - c_l).  Each step reads 9 and writes 9 values per
-//    node; h, p and F never touch DRAM.
-//  * A CTA of BX threads owns BX consecutive columns and marches down a band of
-//    `rows` rows.  Per row r it pulls the populations of row r, forms h on the
-//    row plus a 2-column halo into a 3-row shared ring, then the film pressure
-//    of row r-1 (plus a 1-column halo) into a second ring, then the force and
-//    collision of row r-2, whose populations were kept in registers.  The
-//    radius-2 dependence of grad p on h thus costs 4 extra rows per band and 4
-//    extra columns per strip of recomputed h, all served from L1/L2.
-//  * Loads use the read-only path; stores are aligned and coalesced.
-//  * The rest population is written as h - sum_{l>0} f*_l, which keeps the
-//    local mass of the collision exact up to the rounding of that sum.
+//    node (+ kappa when theta varies); h, p and F never touch DRAM.
+//  * A CTA of BX threads covers BX consecutive columns, one per thread, and
+//    marches down a band of rows; neighbouring CTAs overlap by 4 columns, so
+//    each CTA stores BX - 4 columns and needs no divergent halo work.
+//    March step k: (A) h - href of row r(k) into a 4-row shared ring while
+//    the loads of row r(k+1) are already in flight; one __syncthreads; (B)
+//    the film pressure of row r(k-1) (columns 1 .. BX-2) into a second 4-row
+//    ring, and force + collision + store of row r(k-3) (columns 2 .. BX-3),
+//    whose momentum was kept in registers.  With 4-row rings every shared row is rewritten
+//    only after the barrier that follows its last read, so one barrier per
+//    row suffices.  The radius-2 dependence of grad p on h costs 5 extra rows
+//    per band and 4 extra columns per strip, served from L1/L2.
+//  * Bands are balanced (band b covers rows [b ny / nb, (b+1) ny / nb)) and
+//    alternate their march direction so that shared edge rows hit in L2.
+//  * Plane 0 stores f_0 - href (see tflbm_internal.h).  The rest population
+//    is written as (h - href) - sum_{l>0} f*_l, and the exact rounding
+//    residuals of that subtraction and of the pull sum (error-free TwoSum)
+//    are returned to the opposite pair (1, 5), so in FP32 the collision
+//    conserves local mass up to roundings of the small moving populations.
 #pragma once
 #include <type_traits>
 
@@ -32,173 +40,201 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-template <typename T> __device__ __forceinline__ T rcp(T x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
+// a / b: CUDA's fast single-precision division (within 2 ulp) in FP32, the
+// IEEE division in FP64.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
-// r^n for integer n >= 0 by binary powering (n is uniform across the CTA).
+// r^n for 0 <= n < 64 by binary powering over a fixed number of bits (no
+// data-dependent branches; n is uniform).
 template <typename T>
 __device__ __forceinline__ T ipow(T r, int n)
 {
     T out = T(1), b = r;
-    while (n) {
-        if (n & 1) out *= b;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if ((n >> i) & 1) out *= b;
         b *= b;
-        n >>= 1;
     }
     return out;
 }
 
-template <typename S> __device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
-
-// Pull the nine populations arriving at column x of row `row0` (row offsets
-// already multiplied by the pitch; rowm = row above in -y, rowp = row in +y).
-// Order of Eq. (speeds): 1 (1,0) 2 (1,1) 3 (0,1) 4 (-1,1) 5 (-1,0) 6 (-1,-1)
-// 7 (0,-1) 8 (1,-1); population l at x comes from x - c_l.
-template <typename S, typename T>
-__device__ __forceinline__ void pull9(const S* __restrict__ f, long long plane, long long rowm,
-                                      long long row0, long long rowp, int x, int xm, int xp,
-                                      T (&v)[9])
+// (hstar/h)^n - (hstar/h)^m from r = hstar/h; (3, 2) without the loop.
+template <typename T>
+__device__ __forceinline__ T fdisj(T r, int n, int m)
 {
-    v[0] = T(ldro(f + row0 + x));
-    v[1] = T(ldro(f + plane + row0 + xm));
-    v[2] = T(ldro(f + 2 * plane + rowm + xm));
-    v[3] = T(ldro(f + 3 * plane + rowm + x));
-    v[4] = T(ldro(f + 4 * plane + rowm + xp));
-    v[5] = T(ldro(f + 5 * plane + row0 + xp));
-    v[6] = T(ldro(f + 6 * plane + rowp + xp));
-    v[7] = T(ldro(f + 7 * plane + rowp + x));
-    v[8] = T(ldro(f + 8 * plane + rowp + xm));
+    if (n == 3 && m == 2) return r * r * (r - T(1));
+    return ipow(r, n) - ipow(r, m);
 }
 
-template <typename T>
-__device__ __forceinline__ T sum9(const T (&v)[9])
+template <typename S> __device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
+
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly.  The _rn
+// intrinsics keep the compiler from contracting or reordering the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// Pull the nine populations arriving at column x of row y: i0 = y*pitch + x,
+// im / ip the same row offset for the wrapped columns x-1 / x+1, dm / dp the
+// row steps to rows y-1 / y+1 (wrapped, in elements).  32-bit offsets: the
+// host checks 9 * plane < 2^31.  Order of Eq. (speeds): 1 (1,0) 2 (1,1)
+// 3 (0,1) 4 (-1,1) 5 (-1,0) 6 (-1,-1) 7 (0,-1) 8 (1,-1); population l at x
+// comes from x - c_l.
+template <typename S, typename T>
+__device__ __forceinline__ void pull9(const S* __restrict__ f, int plane, int i0, int im, int ip,
+                                      int dm, int dp, T (&v)[9])
+{
+    v[0] = T(ldro(f + i0));
+    v[1] = T(ldro(f + (plane + im)));
+    v[2] = T(ldro(f + (2 * plane + im + dm)));
+    v[3] = T(ldro(f + (3 * plane + i0 + dm)));
+    v[4] = T(ldro(f + (4 * plane + ip + dm)));
+    v[5] = T(ldro(f + (5 * plane + ip)));
+    v[6] = T(ldro(f + (6 * plane + ip + dp)));
+    v[7] = T(ldro(f + (7 * plane + i0 + dp)));
+    v[8] = T(ldro(f + (8 * plane + im + dp)));
+}
+
+// dh = sum_l v_l with v_0 = f_0 - href: the moving populations are summed
+// first (they are small), the final addition is error-free, so the exact sum
+// of the nine inputs is dh + err up to roundings of the small partial sums.
+template <typename T>
+__device__ __forceinline__ T sum9(const T (&v)[9], T& err)
+{
+    const T m = ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
+    T dh;
+    two_sum(v[0], m, dh, err);
+    return dh;
 }
 
 // Film pressure p = -gamma (lap h + pi_sign kappa f(h)) at one node from the
-// 3x3 neighbourhood of h in the shared ring (rows n = +y, c, s = -y).
+// 3x3 neighbourhood of dh = h - href in the shared ring (rows n = +y, c,
+// s = -y); the Laplacian is taken on dh, in which the offset cancels exactly.
+// ih = 1/h of the node.
 template <typename T>
 __device__ __forceinline__ T film_pressure(const T* hn, const T* hc, const T* hs_, int j, T kap,
-                                           const Consts<T>& C, bool disj)
+                                           T ih, const Consts<T>& C, bool disj)
 {
     const T axis = (hc[j - 1] + hc[j + 1]) + (hn[j] + hs_[j]);
     const T diag = (hn[j - 1] + hn[j + 1]) + (hs_[j - 1] + hs_[j + 1]);
-    const T h = hc[j];
-    T lap = (T(4) * axis + diag - T(20) * h) * T(1.0 / 6.0);
-    if (disj) {
-        const T r = C.hstar * rcp(h);
-        lap += C.pi_sgn * kap * (ipow(r, C.n_exp) - ipow(r, C.m_exp));
-    }
+    T lap = (T(4) * axis + diag - T(20) * hc[j]) * T(1.0 / 6.0);
+    if (disj) lap += C.pi_sgn * kap * fdisj(C.hstar * ih, C.n_exp, C.m_exp);
     return -C.gamma * lap;
 }
 
 template <typename S, typename T, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX)
+__global__ void __launch_bounds__(BX, OMEGA1 ? 1024 / BX : 1)
 k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ kappa,
-       const Geom G, const Consts<T> C, const int rows)
+       const Geom G, const Consts<T> C)
 {
-    constexpr int NW = BX / 32;
-    __shared__ T hsm[3][BX + 4];  // h of rows r, r-1, r-2 (ring), columns x0-2 .. x0+W+1
-    __shared__ T psm[3][BX + 2];  // p of rows r-1, r-2, r-3 (ring), columns x0-1 .. x0+W
+    constexpr int W = BX - 4;     // output columns per CTA
+    __shared__ T hsm[4][BX];      // h - href ring: slot t = column x0 - 2 + t
+    __shared__ T psm[4][BX];      // p ring, same columns
 
     const int t = threadIdx.x;
-    const int nx = G.nx, ny = G.ny;
-    const long long plane = G.plane, pitch = G.pitch;
-    const int x0 = blockIdx.x * BX;
-    const int weff = min(BX, nx - x0);
-    const bool own = t < weff;
-    const int ybeg = blockIdx.y * rows;
-    const int yend = min(ybeg + rows, ny);
+    const int nx = G.nx, ny = G.ny, pitch = G.pitch;
+    const int plane = (int)G.plane;
+    const int x0 = blockIdx.x * W;                 // first output column
+    const int weff = min(W, nx - x0);              // output columns of this CTA
+    const bool hcol = t < weff + 4;                // forms h
+    const bool pcol = t >= 1 && t < weff + 3;      // forms p
+    const bool ocol = t >= 2 && t < weff + 2;      // collides and stores
+    const int ybeg = (int)(((long long)blockIdx.y * ny) / gridDim.y);
+    const int yend = (int)(((long long)(blockIdx.y + 1) * ny) / gridDim.y);
     const bool disj = KFIELD || C.kappa_u != T(0);
 
-    // Halo roles, spread over warps: 0..3 compute h at columns x0-2, x0-1,
-    // x0+W, x0+W+1; 4..5 compute p at columns x0-1, x0+W.
-    int role = -1;
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-        if (t == (q % NW) * 32 + q / NW) role = q;
-    int hcol = x0, hslot = 0;
-    if (role == 0) { hcol = x0 - 2; hslot = 0; }
-    else if (role == 1) { hcol = x0 - 1; hslot = 1; }
-    else if (role == 2) { hcol = x0 + weff; hslot = weff + 2; }
-    else if (role == 3) { hcol = x0 + weff + 1; hslot = weff + 3; }
-    else if (role == 4) { hcol = x0 - 1; hslot = 1; }         // hs slot; p slot = hslot - 1
-    else if (role == 5) { hcol = x0 + weff; hslot = weff + 2; }
-    hcol = wrap_index(hcol, nx);
-    const int hxm = wrap_index(hcol - 1, nx), hxp = wrap_index(hcol + 1, nx);
-
-    const int x = own ? x0 + t : x0;
+    const int x = wrap_index(x0 - 2 + t, nx);
     const int xm = wrap_index(x - 1, nx), xp = wrap_index(x + 1, nx);
 
-    // rolling wrapped row indices of rows r-1, r, r+1
-    int rm = wrap_index(ybeg - 3, ny), r0 = wrap_index(ybeg - 2, ny), rp = wrap_index(ybeg - 1, ny);
+    // March direction: even bands go +y, odd bands -y, so two neighbouring
+    // bands read the rows around their common edge at the same time (both at
+    // the start or both at the end of the kernel) and the second read hits L2.
+    // March step k forms h of row r(k) = r0 + k dir, the pressure of row
+    // r(k-1) and collides row r(k-3), for k = 0 .. R+4 (R = band rows).
+    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    const int R = yend - ybeg;
+    const int rstart = dir > 0 ? ybeg - 2 : yend + 1;
 
-    T fv[3][9];
-    T jxv[3], jyv[3], ihv[3];
+    // wrapped indices of rows r(k-1), r(k), r(k+1), r(k+2)
+    int wm1 = wrap_index(rstart - dir, ny), w0 = wrap_index(rstart, ny);
+    int w1 = wrap_index(rstart + dir, ny), w2 = wrap_index(rstart + 2 * dir, ny);
+
+    // pulled populations of the next row, kappa of the next pressure row,
+    // and per-row values kept until the row is collided three rows later
+    T v[9];
+    T kap_n = C.kappa_u;
+    T fv[4][9];
+    T jxv[4], jyv[4], ihv[4], erv[4];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) { jxv[s] = jyv[s] = ihv[s] = T(0); }
+    for (int s = 0; s < 4; ++s) { jxv[s] = jyv[s] = ihv[s] = erv[s] = T(0); }
 
     const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0), sixth = T(1.0 / 6.0);
     const T one_m_omega = T(1) - C.omega;
     const T d6 = T(6) * C.delta, d3sq = T(3) * C.delta * C.delta;
 
-    auto body = [&](auto stage_c, int r) {
-        constexpr int s = decltype(stage_c)::value;   // slot of row r
-        constexpr int s1 = (s + 2) % 3;               // slot of row r-1
-        constexpr int s2 = (s + 1) % 3;               // slot of row r-2 (and r+1)
-        const long long om = (long long)rm * pitch, o0 = (long long)r0 * pitch,
-                        op = (long long)rp * pitch;
-        // (1) pull row r: h into the ring, momentum into registers
-        if (own) {
-            T v[9];
-            pull9<S, T>(fin, plane, om, o0, op, x, xm, xp, v);
-            hsm[s][t + 2] = sum9(v);
+    // pull row w whose neighbours in march order are wb (behind) and wa (ahead)
+    auto pull_row = [&](int wb, int w, int wa) {
+        const int r0 = w * pitch;
+        const int below = (dir > 0 ? wb : wa) - w, above = (dir > 0 ? wa : wb) - w;
+        pull9<S, T>(fin, plane, r0 + x, r0 + xm, r0 + xp, below * pitch, above * pitch, v);
+    };
+    // prologue: loads of the first h row r(0) and kappa of row r(-1)
+    if (hcol) pull_row(wm1, w0, w1);
+    if (KFIELD && pcol) kap_n = kappa[(long long)wm1 * nx + x];
+
+    auto body = [&](auto stage_c, int k) {
+        constexpr int s = decltype(stage_c)::value;  // slot of row r(k) (and r(k-4))
+        constexpr int s1 = (s + 3) & 3;              // slot of row r(k-1)
+        constexpr int s2 = (s + 2) & 3;              // slot of row r(k-2)
+        constexpr int s3 = (s + 1) & 3;              // slot of row r(k-3)
+        // ---- (A) h of row r(k); the loads of row r(k+1) go out before anything waits
+        const T kap = kap_n;  // kappa of row r(k-1), loaded last step
+        if (hcol && k <= R + 3) {
+            hsm[s][t] = sum9(v, erv[s]);
             jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
             jyv[s] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
             if (!OMEGA1) {
 #pragma unroll
                 for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
             }
-        }
-        if (role >= 0 && role < 4) {
-            T v[9];
-            pull9<S, T>(fin, plane, om, o0, op, hcol, hxm, hxp, v);
-            hsm[s][hslot] = sum9(v);
+            if (k + 1 <= R + 3) pull_row(w0, w1, w2);
+            if (KFIELD && pcol) kap_n = kappa[(long long)w0 * nx + x];
         }
         __syncthreads();
-        // (2) film pressure of row r-1 (needs h rows r-2 .. r)
-        if (r >= ybeg) {
-            const int q = rm;  // wrapped index of row r-1
-            if (own) {
-                const T kap = KFIELD ? kappa[(long long)q * nx + x] : C.kappa_u;
-                psm[s1][t + 1] = film_pressure(hsm[s], hsm[s1], hsm[s2], t + 2, kap, C, disj);
-                ihv[s1] = rcp(hsm[s1][t + 2]);
-            }
-            if (role >= 4) {
-                const T kap = KFIELD ? kappa[(long long)q * nx + hcol] : C.kappa_u;
-                psm[s1][hslot - 1] = film_pressure(hsm[s], hsm[s1], hsm[s2], hslot, kap, C, disj);
-            }
+        // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
+        if (pcol && k >= 2 && k <= R + 3) {
+            const T ih = fdiv(T(1), hsm[s1][t] + C.href);
+            ihv[s1] = ih;
+            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj);
         }
-        __syncthreads();
-        // (3) force and collision of row r-2 (needs p rows r-3 .. r-1)
-        if (r >= ybeg + 2 && own) {
-            const int o = r - 2;  // inside [ybeg, yend), no wrap
-            const T* pn = psm[s1];
-            const T* pc = psm[s2];
-            const T* ps = psm[s];
-            const int j = t + 1;
+        // ---- (B2) force, collision and store of row r(k-3) (needs p rows r(k-4) .. r(k-2))
+        if (ocol && k >= 5) {
+            const int o = rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
+            const T* pn = dir > 0 ? psm[s2] : psm[s];  // row o + 1
+            const T* pcr = psm[s3];
+            const T* ps = dir > 0 ? psm[s] : psm[s2];  // row o - 1
             // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
-            const T gpx = (pc[j + 1] - pc[j - 1]) * third
-                        + ((pn[j + 1] - pn[j - 1]) + (ps[j + 1] - ps[j - 1])) * twelfth;
-            const T gpy = (pn[j] - ps[j]) * third
-                        + ((pn[j + 1] - ps[j + 1]) + (pn[j - 1] - ps[j - 1])) * twelfth;
-            const T h = hsm[s2][t + 2];
-            const T ih = ihv[s2];
-            const T jx = jxv[s2], jy = jyv[s2];
-            // Eqs. (force), (forcefric), (alphafric): nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
-            const T fr = C.nu6 * rcp(h * (T(2) * h + d6) + d3sq);
+            const T gpx = (pcr[t + 1] - pcr[t - 1]) * third
+                        + ((pn[t + 1] - pn[t - 1]) + (ps[t + 1] - ps[t - 1])) * twelfth;
+            const T gpy = (pn[t] - ps[t]) * third
+                        + ((pn[t + 1] - ps[t + 1]) + (pn[t - 1] - ps[t - 1])) * twelfth;
+            const T dh = hsm[s3][t];
+            const T h = dh + C.href;
+            const T ih = ihv[s3];
+            const T jx = jxv[s3], jy = jyv[s3];
+            // Eqs. (force), (forcefric), (alphafric):
+            // nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
+            const T fr = fdiv(C.nu6, h * (T(2) * h + d6) + d3sq);
             const T Fx = h * (C.gx - gpx) - fr * jx;
             const T Fy = h * (C.gy - gpy) - fr * jy;
             // Eq. (equilibria) with e^2 = 1, written as S +- D per pair of
@@ -225,7 +261,7 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
                 const T Da = (jx + jy) * twelfth, Db = (jy - jx) * twelfth;
                 const T Qx = Fx * third, Qy = Fy * third;
                 const T Qa = (Fx + Fy) * twelfth, Qb = (Fy - Fx) * twelfth;
-                const T(&f)[9] = fv[s2];
+                const T(&f)[9] = fv[s3];
                 o1 = one_m_omega * f[1] + w * (Sx + Dx) + Qx;
                 o5 = one_m_omega * f[5] + w * (Sx - Dx) - Qx;
                 o3 = one_m_omega * f[3] + w * (Sy + Dy) + Qy;
@@ -235,8 +271,18 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
                 o4 = one_m_omega * f[4] + w * (Sb + Db) + Qb;
                 o8 = one_m_omega * f[8] + w * (Sb - Db) - Qb;
             }
-            const T o0v = h - (((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8)));
-            S* out = fout + (long long)o * pitch + x;
+            // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l;
+            // the exact rounding residuals of the pull sum and of this
+            // subtraction go to the opposite pair (1, 5), half each, so the
+            // stored populations sum to the pulled ones (mass conserved to
+            // roundings of small values) and the momentum is untouched.
+            const T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
+            T o0v, e2;
+            two_sum(dh, -osum, o0v, e2);
+            const T half_r = (erv[s3] + e2) * T(0.5);
+            o1 += half_r;
+            o5 += half_r;
+            S* out = fout + (o * pitch + x);
             out[0] = S(o0v);
             out[plane] = S(o1);
             out[2 * plane] = S(o2);
@@ -248,19 +294,23 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
             out[8 * plane] = S(o8);
         }
         // advance the wrapped row window
-        rm = r0;
-        r0 = rp;
-        rp = (rp + 1 == ny) ? 0 : rp + 1;
+        wm1 = w0;
+        w0 = w1;
+        w1 = w2;
+        w2 += dir;
+        w2 = w2 == ny ? 0 : (w2 < 0 ? ny - 1 : w2);
     };
 
-    const int last = yend + 1;
-    for (int r = ybeg - 2;;) {
-        body(std::integral_constant<int, 0>{}, r);
-        if (++r > last) break;
-        body(std::integral_constant<int, 1>{}, r);
-        if (++r > last) break;
-        body(std::integral_constant<int, 2>{}, r);
-        if (++r > last) break;
+    const int last = R + 4;
+    for (int k = 0;;) {
+        body(std::integral_constant<int, 0>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 1>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 2>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 3>{}, k);
+        if (++k > last) break;
     }
 }
 
@@ -268,16 +318,31 @@ template <typename S, typename T, int BX>
 cudaError_t launch_step_bx(const S* fin, S* fout, const T* kappa, const Geom& G,
                            const Consts<T>& C, int rows, cudaStream_t st)
 {
-    dim3 grid((G.nx + BX - 1) / BX, (G.ny + rows - 1) / rows);
+    int bands = (G.ny + rows - 1) / rows;
+    if (bands > 65535) bands = 65535;
+    dim3 grid((G.nx + BX - 5) / (BX - 4), bands);
     const bool om1 = (C.omega == T(1));
     if (kappa) {
-        if (om1) k_step<S, T, BX, true, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C, rows);
-        else k_step<S, T, BX, false, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C, rows);
+        if (om1) k_step<S, T, BX, true, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
+        else k_step<S, T, BX, false, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
     } else {
-        if (om1) k_step<S, T, BX, true, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C, rows);
-        else k_step<S, T, BX, false, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C, rows);
+        if (om1) k_step<S, T, BX, true, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
+        else k_step<S, T, BX, false, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
     }
     return cudaGetLastError();
+}
+
+// Resident CTAs per SM of one instantiation (for sizing the grid).
+template <typename S, typename T, int BX>
+int blocks_per_sm_bx(bool omega1, bool kfield)
+{
+    int n = 0;
+    cudaError_t e;
+    if (kfield) e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, true, true>, BX, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, false, true>, BX, 0);
+    else e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, true, false>, BX, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, false, false>, BX, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace tflbm

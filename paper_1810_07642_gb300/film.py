@@ -91,12 +91,13 @@ class ThinFilm:
         return L.tf_lbm_check(self.handle, self._st)
 
     def get_state(self):
-        f = torch.empty((9, self.ny, self.nx), dtype=self.tdtype, device=self.device)
+        """Post-streaming populations f_l(x, t) as a float64 (9, ny, nx) tensor."""
+        f = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)
         L.tf_lbm_get_state(self.handle, f.data_ptr(), self._st)
         return f
 
     def set_state(self, f):
-        f = torch.as_tensor(f).to(device=self.device, dtype=self.tdtype).contiguous()
+        f = torch.as_tensor(f).to(device=self.device, dtype=torch.float64).contiguous()
         L.tf_lbm_set_state(self.handle, f.data_ptr(), self._st)
         self._keep = (f,)
 

