@@ -153,6 +153,27 @@ int64_t tf_lbm_time(const tf_lbm_handle* H);
 int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out);
 int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in);
 
+/* Largest n accepted by tf_lbm_sum_noalloc: 4096 blocks of 16384 elements. */
+#define TF_LBM_NOALLOC_MAX_ELEMS 67108864LL
+
+/* Compensated (Neumaier) double-precision sum of x[0 .. n) written to *out,
+ * with no memory allocation of any kind.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory, e.g. code inside a host
+ * application that owns the device memory budget through its own pool, or
+ * loops that cannot afford cudaMalloc's possible device-wide synchronisation.
+ * Summing the state exported by tf_lbm_get_state gives the total volume that
+ * tf_lbm_mass reports, without a handle-side allocation.
+ *   x:   device (or managed) array of n doubles; may be NULL when n == 0.
+ *   n:   0 <= n <= TF_LBM_NOALLOC_MAX_ELEMS, else TF_LBM_ERR_ARG.
+ *   out: device (or managed) double; written asynchronously on `stream`.
+ * Block partial sums go to a fixed 64 KB file-scope device array that every
+ * GPU loading the library keeps until exit.  Its device address is looked up
+ * on the first call made on each device, so make that first call before any
+ * stream capture.  Calls share the array: calls whose kernels overlap on the
+ * GPU (unordered streams) race and give wrong sums.  Errors are described by
+ * tf_lbm_last_error(NULL). */
+int tf_lbm_sum_noalloc(const double* x, int64_t n, double* out, void* stream);
+
 /* Release everything the handle owns (waits for its device work). NULL ok. */
 void tf_lbm_destroy(tf_lbm_handle* H);
 

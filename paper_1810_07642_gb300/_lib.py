@@ -21,7 +21,9 @@ EXPORTED = [
     "tf_lbm_init", "tf_lbm_step", "tf_lbm_moments", "tf_lbm_pressure_force", "tf_lbm_mass",
     "tf_lbm_check", "tf_lbm_get_state", "tf_lbm_set_state", "tf_lbm_time", "tf_lbm_get_launch",
     "tf_lbm_set_launch", "tf_lbm_destroy", "tf_lbm_last_error", "tf_lbm_version",
+    "tf_lbm_sum_noalloc",
 ]
+TF_LBM_NOALLOC_MAX_ELEMS = 67108864
 
 
 class TfLbmError(RuntimeError):
@@ -83,6 +85,7 @@ def lib():
     L.tf_lbm_last_error.argtypes = [_VP]
     L.tf_lbm_last_error.restype = ctypes.c_char_p
     L.tf_lbm_version.restype = i32
+    L.tf_lbm_sum_noalloc.argtypes = [_VP, i64, _VP, _VP]
     _lib = L
     return L
 
@@ -163,3 +166,9 @@ def tf_lbm_last_error(handle: int | None = None) -> str:
 
 def tf_lbm_version() -> int:
     return int(lib().tf_lbm_version())
+
+
+def tf_lbm_sum_noalloc(x: int, n: int, out: int, stream: int = 0) -> None:
+    """Compensated sum of n device doubles at x into the device double at out,
+    allocating nothing (for callers that may not allocate device memory)."""
+    _check(lib().tf_lbm_sum_noalloc(_VP(x), int(n), _VP(out), _VP(stream)), None)

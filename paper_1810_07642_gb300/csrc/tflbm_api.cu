@@ -176,6 +176,11 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 
 }  // namespace
 
+namespace tflbm {
+// Message for tf_lbm_last_error(NULL) from entry points without a handle.
+void set_thread_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace tflbm
+
 extern "C" {
 
 int32_t tf_lbm_version(void) { return 100; }
