@@ -31,7 +31,7 @@
  *     (0,0) (1,0) (1,1) (0,1) (-1,1) (-1,0) (-1,-1) (0,-1) (1,-1).
  *   - "device" pointers are CUDA device (or managed) memory on the handle's
  *     device.  The element type of h0, theta, and of every field output is
- *     float for TF_LBM_F32 and double for TF_LBM_F64.
+ *     the compute type: double for TF_LBM_F64, float for the others.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls
  *     are asynchronous on it except tf_lbm_mass and tf_lbm_check, which
  *     synchronise it to return a host value.
@@ -52,9 +52,21 @@ extern "C" {
 
 /* storage / compute type of the populations */
 enum {
-    TF_LBM_F32 = 0, /* FP32 storage and arithmetic */
-    TF_LBM_F64 = 1  /* FP64 storage and arithmetic */
+    TF_LBM_F32 = 0,  /* FP32 storage and arithmetic                          */
+    TF_LBM_F64 = 1,  /* FP64 storage and arithmetic                          */
+    TF_LBM_F16 = 2,  /* moving populations in FP16, rest population and all
+                        arithmetic in FP32 (see below)                       */
+    TF_LBM_BF16 = 3  /* as TF_LBM_F16 with BF16 moving populations           */
 };
+/* 16-bit storage (TF_LBM_F16, TF_LBM_BF16).  The rest population carries
+ * almost all of h; it is kept in FP32 as f_0 - href (href = mean of h0).  The
+ * eight moving populations are kept as deviations from the rest equilibrium
+ * at href, f_l - f_eq_l(href, 0), in FP16 scaled by 2^10 or in BF16.  Every
+ * value is decoded to FP32 before use, and the 16-bit rounding of each
+ * collision is folded exactly into the FP32 rest population, so the total
+ * volume changes only by FP32 roundings of f_0 - href.  Bytes per lattice
+ * update: 2 x (4 + 8 x 2) = 40 (+4 with a theta field), against 72 (+4) in
+ * FP32. */
 
 /* return codes */
 enum {
@@ -75,7 +87,7 @@ enum {
 /* Physical and numerical parameters (lattice units, dx = dt = 1). */
 typedef struct tf_lbm_params {
     int32_t nx, ny;       /* periodic lattice size, each >= 1                   */
-    int32_t dtype;        /* TF_LBM_F32 or TF_LBM_F64                           */
+    int32_t dtype;        /* TF_LBM_F32, TF_LBM_F64, TF_LBM_F16 or TF_LBM_BF16   */
     int32_t n_exp, m_exp; /* exponents of Eq. (disjoiningP), n != m, >= 1     */
     int32_t pi_sign;      /* +1 physical (default) or -1 printed sign of Pi     */
     double tau;           /* relaxation time, > 1/2; omega = 1/tau             */

@@ -11,7 +11,7 @@ import os
 
 from . import build as _build
 
-TF_LBM_F32, TF_LBM_F64 = 0, 1
+TF_LBM_F32, TF_LBM_F64, TF_LBM_F16, TF_LBM_BF16 = 0, 1, 2, 3
 TF_LBM_OK = 0
 TF_LBM_ERR_ARG, TF_LBM_ERR_CUDA, TF_LBM_ERR_NOMEM = -1, -2, -3
 TF_LBM_ERR_NONFINITE, TF_LBM_ERR_UNSUPPORTED = -4, -5

@@ -1,27 +1,57 @@
-// FP32 instantiations of the fused step (tflbm_step.cuh).
+// FP32 and FP64 instantiations of the fused step (tflbm_step.cuh) and the
+// dispatch over storage types.
 #include "tflbm_step.cuh"
 
 namespace tflbm {
 
-cudaError_t launch_step_f32(const float* fin, float* fout, const float* kappa, const Geom& G,
-                            const Consts<float>& C, const Shape& S, cudaStream_t st)
+cudaError_t launch_step_narrow(int store, const void* fin, void* fout, const void* kappa,
+                               const Geom& G, const Consts<float>& C, const Shape& S,
+                               cudaStream_t st);
+int blocks_per_sm_narrow(int store, int block_x, bool omega1, bool kfield);
+
+template <typename SM, typename T>
+static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, const Geom& G,
+                                const Consts<T>& C, const Shape& S, cudaStream_t st)
 {
+    const T* f0 = (const T*)fin;
+    const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(T));
+    T* g0 = (T*)fout;
+    SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
+    const T* k = (const T*)kappa;
     switch (S.block_x) {
-        case 64: return launch_step_bx<float, float, 64>(fin, fout, kappa, G, C, S.rows, st);
-        case 128: return launch_step_bx<float, float, 128>(fin, fout, kappa, G, C, S.rows, st);
-        case 256: return launch_step_bx<float, float, 256>(fin, fout, kappa, G, C, S.rows, st);
+        case 64: return launch_step_bx<SM, T, 64>(f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 128: return launch_step_bx<SM, T, 128>(f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 256: return launch_step_bx<SM, T, 256>(f0, fm, g0, gm, k, G, C, S.rows, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int step_blocks_per_sm_f32(int block_x, bool omega1, bool kfield)
+cudaError_t launch_step(int store, const void* fin, void* fout, const void* kappa, const Geom& G,
+                        const Consts<float>* C32, const Consts<double>* C64, const Shape& S,
+                        cudaStream_t st)
 {
-    switch (block_x) {
-        case 64: return blocks_per_sm_bx<float, float, 64>(omega1, kfield);
-        case 128: return blocks_per_sm_bx<float, float, 128>(omega1, kfield);
-        case 256: return blocks_per_sm_bx<float, float, 256>(omega1, kfield);
-        default: return 0;
+    switch (store) {
+        case kStoreF32: return launch_typed<float, float>(fin, fout, kappa, G, *C32, S, st);
+        case kStoreF64: return launch_typed<double, double>(fin, fout, kappa, G, *C64, S, st);
+        default: return launch_step_narrow(store, fin, fout, kappa, G, *C32, S, st);
     }
+}
+
+int step_blocks_per_sm(int store, int block_x, bool omega1, bool kfield)
+{
+    if (store == kStoreF32 || store == kStoreF64) {
+        const bool f = store == kStoreF32;
+        switch (block_x) {
+            case 64: return f ? blocks_per_sm_bx<float, float, 64>(omega1, kfield)
+                              : blocks_per_sm_bx<double, double, 64>(omega1, kfield);
+            case 128: return f ? blocks_per_sm_bx<float, float, 128>(omega1, kfield)
+                               : blocks_per_sm_bx<double, double, 128>(omega1, kfield);
+            case 256: return f ? blocks_per_sm_bx<float, float, 256>(omega1, kfield)
+                               : blocks_per_sm_bx<double, double, 256>(omega1, kfield);
+            default: return 0;
+        }
+    }
+    return blocks_per_sm_narrow(store, block_x, omega1, kfield);
 }
 
 }  // namespace tflbm

@@ -17,7 +17,10 @@ using namespace tflbm;
 struct tf_lbm_handle {
     tf_lbm_params p;
     int device = 0;
-    size_t esize = 4;
+    size_t esize = 4;          // bytes of the compute type (plane 0, fields)
+    size_t msize = 4;          // bytes of one stored moving population
+    bool dbl = false;          // compute type is double
+    StoreDesc desc{};          // storage encoding (for the auxiliary kernels)
     Geom G{};
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;               // buf[cur] holds the post-collision populations of step t-1
@@ -98,6 +101,10 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.kappa_u = T(H->kappa_u);
     C.pi_sgn = T(H->p.pi_sign);
     C.href = T(H->href);
+    C.mscale = T(H->desc.mscale);
+    C.minv = T(H->desc.minv);
+    C.r_axis = T(H->desc.r_axis);
+    C.r_diag = T(H->desc.r_diag);
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
     return C;
@@ -105,13 +112,10 @@ Consts<T> make_consts(const tf_lbm_handle* H)
 
 cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
 {
-    const void* fin = H->buf[from];
-    void* fout = H->buf[from ^ 1];
-    if (H->p.dtype == TF_LBM_F32)
-        return launch_step_f32((const float*)fin, (float*)fout, (const float*)H->kappa, H->G,
-                               make_consts<float>(H), H->shape, st);
-    return launch_step_f64((const double*)fin, (double*)fout, (const double*)H->kappa, H->G,
-                           make_consts<double>(H), H->shape, st);
+    const Consts<float> c32 = make_consts<float>(H);
+    const Consts<double> c64 = make_consts<double>(H);
+    return launch_step(H->desc.store, H->buf[from], H->buf[from ^ 1], H->kappa, H->G, &c32, &c64,
+                       H->shape, st);
 }
 
 void drop_graphs(tf_lbm_handle* H)
@@ -135,7 +139,8 @@ int validate(const tf_lbm_params* p)
     if (p->nx < 1 || p->ny < 1) return bad("nx and ny must be >= 1");
     if (p->ny > 65535) return bad("ny must be <= 65535");
     if ((long long)p->nx * p->ny > (1LL << 31)) return bad("nx * ny must be <= 2^31");
-    if (p->dtype != TF_LBM_F32 && p->dtype != TF_LBM_F64) return bad("dtype must be TF_LBM_F32 or TF_LBM_F64");
+    if (p->dtype != TF_LBM_F32 && p->dtype != TF_LBM_F64 && p->dtype != TF_LBM_F16 && p->dtype != TF_LBM_BF16)
+        return bad("dtype must be TF_LBM_F32, TF_LBM_F64, TF_LBM_F16 or TF_LBM_BF16");
     if (!(p->tau > 0.5)) return bad("tau must be > 1/2");
     if (!(p->hstar > 0.0)) return bad("hstar must be > 0");
     if (!(p->delta >= 0.0)) return bad("delta must be >= 0");
@@ -152,6 +157,16 @@ int validate(const tf_lbm_params* p)
 // band height that makes the grid one full wave of resident CTAs (all bands
 // do the same work, so a partial second wave would idle most SMs), but no
 // shorter than 16 rows: each band spends 5 warm-up rows.
+int store_of(int dtype)
+{
+    switch (dtype) {
+        case TF_LBM_F64: return kStoreF64;
+        case TF_LBM_F16: return kStoreF16;
+        case TF_LBM_BF16: return kStoreBF16;
+        default: return kStoreF32;
+    }
+}
+
 Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 {
     Shape s;
@@ -162,8 +177,7 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool om1 = p.tau == 1.0;
-    int occ = p.dtype == TF_LBM_F32 ? step_blocks_per_sm_f32(s.block_x, om1, kfield)
-                                    : step_blocks_per_sm_f64(s.block_x, om1, kfield);
+    int occ = step_blocks_per_sm(store_of(p.dtype), s.block_x, om1, kfield);
     if (occ < 1) occ = 4;
     int bands = occ * sms / strips;
     if (bands < 1) bands = 1;
@@ -205,13 +219,16 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     H->p = *params;
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetDevice(&H->device);
-    H->esize = params->dtype == TF_LBM_F32 ? 4 : 8;
-    const int align = 128 / (int)H->esize;  // rows start on 128-byte boundaries
+    H->desc.store = store_of(params->dtype);
+    H->dbl = params->dtype == TF_LBM_F64;
+    H->esize = H->dbl ? 8 : 4;
+    H->msize = (params->dtype == TF_LBM_F16 || params->dtype == TF_LBM_BF16) ? 2 : H->esize;
+    const int align = 128 / (int)H->msize;  // rows of every plane start on 128-byte boundaries
     H->G.nx = params->nx;
     H->G.ny = params->ny;
     H->G.pitch = (params->nx + align - 1) / align * align;
     H->G.plane = (long long)params->ny * H->G.pitch;
-    if (9LL * H->G.plane >= (1LL << 31)) {
+    if (9LL * H->G.plane >= (1LL << 31)) {  // the step kernel uses 32-bit element offsets
         delete H;
         return fail(nullptr, TF_LBM_ERR_UNSUPPORTED,
                     "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
@@ -224,7 +241,7 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
         tf_lbm_destroy(H);
         return code;
     };
-    const size_t bytes = 9ull * H->G.plane * H->esize;
+    const size_t bytes = (size_t)H->G.plane * (H->esize + 8 * H->msize);
     cudaError_t e;
     for (int b = 0; b < 2; ++b) {
         if ((e = cudaMalloc(&H->buf[b], bytes)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc populations"));
@@ -242,30 +259,33 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     const long long n = (long long)params->nx * params->ny;
     if (theta) {
         if ((e = cudaMalloc(&H->kappa, n * H->esize)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc kappa"));
-        e = params->dtype == TF_LBM_F32
-                ? launch_kappa_f32((float*)H->kappa, (const float*)theta, params->nx, params->ny,
-                                   params->n_exp, params->m_exp, params->hstar, st)
-                : launch_kappa_f64((double*)H->kappa, (const double*)theta, params->nx, params->ny,
-                                   params->n_exp, params->m_exp, params->hstar, st);
+        e = aux_kappa(H->dbl, H->kappa, theta, params->nx, params->ny, params->n_exp, params->m_exp,
+                      params->hstar, st);
         if (e != cudaSuccess) return bail(cuda_fail(H, e, "kappa kernel"));
     } else {
         H->kappa_u = (1.0 - cos(params->theta_uniform)) * kscale;
     }
     // reference height: the mean of h0, rounded to the storage type
-    e = params->dtype == TF_LBM_F32
-            ? launch_sum_f32((const float*)h0, n, H->partials, H->nmass, H->result, st)
-            : launch_sum_f64((const double*)h0, n, H->partials, H->nmass, H->result, st);
+    e = aux_sum(H->dbl, h0, n, H->partials, H->nmass, H->result, st);
     if (e != cudaSuccess) return bail(cuda_fail(H, e, "sum kernel"));
     double hsum = 0.0;
     if ((e = cudaMemcpyAsync(&hsum, H->result, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return bail(cuda_fail(H, e, "reading the mean height"));
     const double mean = hsum / (double)n;
-    H->href = params->dtype == TF_LBM_F32 ? (double)(float)mean : mean;
+    H->href = H->dbl ? mean : (double)(float)mean;
     if (!isfinite(H->href)) H->href = 0.0;  // a non-finite h0 is reported by tf_lbm_check
-    e = params->dtype == TF_LBM_F32
-            ? launch_init_f32((float*)H->buf[0], (const float*)h0, H->G, (float)params->g, (float)H->href, st)
-            : launch_init_f64((double*)H->buf[0], (const double*)h0, H->G, params->g, H->href, st);
+    // 16-bit storage of the moving populations: deviations from the rest
+    // equilibrium at href, scaled by 2^10 in FP16 (keeps small deviations out
+    // of the subnormal range; |f_l| up to 64 stays finite), unscaled in BF16.
+    H->desc.href = H->href;
+    H->desc.mscale = params->dtype == TF_LBM_F16 ? 1024.0 : 1.0;
+    H->desc.minv = 1.0 / H->desc.mscale;
+    if (H->msize == 2) {
+        H->desc.r_axis = (double)(float)(params->g * H->href * H->href / 6.0);
+        H->desc.r_diag = (double)(float)(params->g * H->href * H->href / 24.0);
+    }
+    e = aux_init(H->desc, H->buf[0], h0, H->G, params->g, st);
     if (e != cudaSuccess) return bail(cuda_fail(H, e, "init kernel"));
     H->cur = 0;
     *out = H;
@@ -315,11 +335,7 @@ int tf_lbm_moments(tf_lbm_handle* H, void* h, void* ux, void* uy, void* stream)
         (rc = check_dev_ptr(H, uy, "uy", true)))
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_moments_f32((const float*)H->buf[H->cur], (float*)h, (float*)ux, (float*)uy, H->G,
-                                             (float)H->href, st)
-                        : launch_moments_f64((const double*)H->buf[H->cur], (double*)h, (double*)ux, (double*)uy, H->G,
-                                             H->href, st);
+    cudaError_t e = aux_moments(H->desc, H->buf[H->cur], h, ux, uy, H->G, st);
     CK(H, e, "moments kernel");
     return TF_LBM_OK;
 }
@@ -334,16 +350,11 @@ int tf_lbm_pressure_force(tf_lbm_handle* H, void* p, void* fx, void* fy, void* s
     cudaStream_t st = (cudaStream_t)stream;
     const long long n = (long long)H->G.nx * H->G.ny;
     if (!H->diag) CK(H, cudaMalloc(&H->diag, 2 * n * H->esize), "cudaMalloc diagnostics");
-    cudaError_t e;
-    if (H->p.dtype == TF_LBM_F32) {
-        float* s = (float*)H->diag;
-        e = launch_pressure_force_f32((const float*)H->buf[H->cur], (const float*)H->kappa, (float*)p,
-                                      (float*)fx, (float*)fy, s, s + n, H->G, make_consts<float>(H), st);
-    } else {
-        double* s = (double*)H->diag;
-        e = launch_pressure_force_f64((const double*)H->buf[H->cur], (const double*)H->kappa, (double*)p,
-                                      (double*)fx, (double*)fy, s, s + n, H->G, make_consts<double>(H), st);
-    }
+    const Consts<float> c32 = make_consts<float>(H);
+    const Consts<double> c64 = make_consts<double>(H);
+    char* sc = (char*)H->diag;
+    cudaError_t e = aux_pressure_force(H->desc, H->buf[H->cur], H->kappa, p, fx, fy, sc, sc + n * H->esize,
+                                       H->G, &c32, &c64, st);
     CK(H, e, "pressure/force kernels");
     return TF_LBM_OK;
 }
@@ -353,9 +364,7 @@ int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream)
     if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
     if (!mass_host) return fail(H, TF_LBM_ERR_ARG, "mass_host must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_mass_f32((const float*)H->buf[H->cur], H->G, H->partials, H->nmass, H->result, st)
-                        : launch_mass_f64((const double*)H->buf[H->cur], H->G, H->partials, H->nmass, H->result, st);
+    cudaError_t e = aux_mass(H->desc, H->buf[H->cur], H->G, H->partials, H->nmass, H->result, st);
     CK(H, e, "mass kernels");
     CK(H, cudaMemcpyAsync(mass_host, H->result, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     CK(H, cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -370,9 +379,7 @@ int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream)
     if (!status_host) return fail(H, TF_LBM_ERR_ARG, "status_host must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     CK(H, cudaMemsetAsync(H->flag, 0, sizeof(int), st), "cudaMemsetAsync");
-    cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_check_f32((const float*)H->buf[H->cur], H->G, (float)H->href, H->flag, st)
-                        : launch_check_f64((const double*)H->buf[H->cur], H->G, H->href, H->flag, st);
+    cudaError_t e = aux_check(H->desc, H->buf[H->cur], H->G, H->flag, st);
     CK(H, e, "check kernel");
     int v = 0;
     CK(H, cudaMemcpyAsync(&v, H->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
@@ -387,9 +394,7 @@ int tf_lbm_get_state(tf_lbm_handle* H, void* f, void* stream)
     int rc;
     if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_get_state_f32((const float*)H->buf[H->cur], (double*)f, H->G, (float)H->href, st)
-                        : launch_get_state_f64((const double*)H->buf[H->cur], (double*)f, H->G, H->href, st);
+    cudaError_t e = aux_get_state(H->desc, H->buf[H->cur], (double*)f, H->G, st);
     CK(H, e, "get_state kernel");
     return TF_LBM_OK;
 }
@@ -400,9 +405,7 @@ int tf_lbm_set_state(tf_lbm_handle* H, const void* f, void* stream)
     int rc;
     if ((rc = check_dev_ptr(H, f, "f", false))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = H->p.dtype == TF_LBM_F32
-                        ? launch_set_state_f32((float*)H->buf[H->cur], (const double*)f, H->G, (float)H->href, st)
-                        : launch_set_state_f64((double*)H->buf[H->cur], (const double*)f, H->G, H->href, st);
+    cudaError_t e = aux_set_state(H->desc, H->buf[H->cur], (const double*)f, H->G, st);
     CK(H, e, "set_state kernel");
     return TF_LBM_OK;
 }
@@ -424,8 +427,7 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
     if (!in) return fail(H, TF_LBM_ERR_ARG, "launch is NULL");
     const int bx = in->block_x;
-    const bool ok_bx = H->p.dtype == TF_LBM_F32 ? (bx == 64 || bx == 128 || bx == 256) : (bx == 64 || bx == 128);
-    if (!ok_bx) return fail(H, TF_LBM_ERR_ARG, "block_x must be 64, 128 or 256 (64 or 128 for FP64)");
+    if (bx != 64 && bx != 128 && bx != 256) return fail(H, TF_LBM_ERR_ARG, "block_x must be 64, 128 or 256");
     if (in->rows < 1 || in->rows > 65535) return fail(H, TF_LBM_ERR_ARG, "rows must be in [1, 65535]");
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");

@@ -1,10 +1,17 @@
 // Auxiliary kernels of the thin-film D2Q9 library: kappa field, initial
 // populations, moments, film pressure and force (diagnostic), compensated
-// mass, state scan and state import/export.  The stored buffer holds
-// post-collision (pre-streaming) populations B_l, so the post-streaming
-// populations of the current time are f_l(x) = B_l(x - c_l); plane 0 stores
-// B_0 - href (the reference height convention of tflbm_internal.h).
+// mass, state scan and state import/export.
+//
+// The stored buffer holds post-collision (pre-streaming) populations B_l, so
+// the post-streaming populations of the current time are f_l(x) = B_l(x - c_l).
+// Plane 0 stores B_0 - href in the compute type; the 8 moving planes follow in
+// the storage type (the compute type, or a 16-bit encoding, see Consts in
+// tflbm_internal.h).  All kernels here go through the Pops accessor below.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "tflbm_internal.h"
 
@@ -20,17 +27,65 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-// Post-streaming populations at (x, y), with the rest population restored.
-template <typename T>
-__device__ __forceinline__ void pull_at(const T* __restrict__ f, const Geom& G, int x, int y,
-                                        T href, T (&v)[9])
+__device__ __forceinline__ float cvt(float q) { return q; }
+__device__ __forceinline__ double cvt(double q) { return q; }
+__device__ __forceinline__ float cvt(__half q) { return __half2float(q); }
+__device__ __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
+template <typename SM> __device__ __forceinline__ SM enc(float v);
+template <> __device__ __forceinline__ __half enc<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 enc<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Read / write access to one population buffer.
+template <typename T, typename SM>
+struct Pops {
+    T* f0;       // plane 0: f_0 - href
+    SM* fm;      // moving planes 1..8
+    long long plane;
+    int pitch;
+    T href, mscale, minv, r_axis, r_diag;
+
+    __device__ __forceinline__ long long at(int y, int x) const { return (long long)y * pitch + x; }
+    // the stored value of plane l at element i, decoded (plane 0: f_0 - href)
+    __device__ __forceinline__ T raw(int l, long long i) const
+    {
+        if (l == 0) return f0[i];
+        const SM q = fm[(l - 1) * plane + i];
+        if constexpr (std::is_same<SM, T>::value) return q;
+        else return fmaf(cvt(q), minv, (l & 1) ? r_axis : r_diag);
+    }
+    __device__ __forceinline__ T full(int l, long long i) const { return l == 0 ? raw(0, i) + href : raw(l, i); }
+    // store the population value v (plane 0: v is f_0 - href)
+    __device__ __forceinline__ void put(int l, long long i, T v) const
+    {
+        if (l == 0) f0[i] = v;
+        else if constexpr (std::is_same<SM, T>::value) fm[(l - 1) * plane + i] = v;
+        else fm[(l - 1) * plane + i] = enc<SM>((v - ((l & 1) ? r_axis : r_diag)) * mscale);
+    }
+};
+
+template <typename T, typename SM>
+Pops<T, SM> make_pops(const void* buf, const Geom& G, const StoreDesc& D)
+{
+    Pops<T, SM> P;
+    P.f0 = (T*)buf;
+    P.fm = (SM*)((char*)buf + G.plane * sizeof(T));
+    P.plane = G.plane;
+    P.pitch = G.pitch;
+    P.href = T(D.href);
+    P.mscale = T(D.mscale);
+    P.minv = T(D.minv);
+    P.r_axis = T(D.r_axis);
+    P.r_diag = T(D.r_diag);
+    return P;
+}
+
+// Post-streaming populations at (x, y).
+template <typename T, typename SM>
+__device__ __forceinline__ void pull_at(const Pops<T, SM>& P, const Geom& G, int x, int y, T (&v)[9])
 {
 #pragma unroll
-    for (int l = 0; l < 9; ++l) {
-        const int xs = wrapi(x - kCx[l], G.nx), ys = wrapi(y - kCy[l], G.ny);
-        v[l] = f[l * G.plane + (long long)ys * G.pitch + xs];
-    }
-    v[0] += href;
+    for (int l = 0; l < 9; ++l)
+        v[l] = P.full(l, P.at(wrapi(y - kCy[l], G.ny), wrapi(x - kCx[l], G.nx)));
 }
 
 template <typename T>
@@ -52,8 +107,8 @@ __global__ void k_kappa(T* kappa, const T* theta, long long n, int ne, int me, d
 }
 
 // B_l(x) = f_eq_l(h0(x + c_l), u = 0), so that the pull gives f = f_eq(h0, 0).
-template <typename T>
-__global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g, T href)
+template <typename T, typename SM>
+__global__ void k_init(Pops<T, SM> P, const T* __restrict__ h0, Geom G, T g)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -63,21 +118,21 @@ __global__ void k_init(T* f, const T* __restrict__ h0, Geom G, T g, T href)
         const T h = h0[(long long)wrapi(y + kCy[l], G.ny) * G.nx + wrapi(x + kCx[l], G.nx)];
         const T gh2 = g * h * h;
         T v;
-        if (l == 0) v = (h - href) - T(5.0 / 6.0) * gh2;
+        if (l == 0) v = (h - P.href) - T(5.0 / 6.0) * gh2;
         else if (l & 1) v = gh2 * T(1.0 / 6.0);
         else v = gh2 * T(1.0 / 24.0);
-        f[l * G.plane + (long long)y * G.pitch + x] = v;
+        P.put(l, P.at(y, x), v);
     }
 }
 
-template <typename T>
-__global__ void k_moments(const T* __restrict__ f, T* h, T* ux, T* uy, Geom G, T href)
+template <typename T, typename SM>
+__global__ void k_moments(Pops<T, SM> P, T* h, T* ux, T* uy, Geom G)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, href, v);
+    pull_at(P, G, x, y, v);
     moments9(v, hh, jx, jy);
     const long long i = (long long)y * G.nx + x;
     if (h) h[i] = hh;
@@ -86,14 +141,14 @@ __global__ void k_moments(const T* __restrict__ f, T* h, T* ux, T* uy, Geom G, T
 }
 
 // Diagnostic film pressure and force, in three plain passes.
-template <typename T>
-__global__ void k_pf_h(const T* __restrict__ f, T* hbuf, Geom G, Consts<T> C)
+template <typename T, typename SM>
+__global__ void k_pf_h(Pops<T, SM> P, T* hbuf, Geom G)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, C.href, v);
+    pull_at(P, G, x, y, v);
     moments9(v, hh, jx, jy);
     hbuf[(long long)y * G.nx + x] = hh;
 }
@@ -126,24 +181,24 @@ __global__ void k_pf_p(const T* __restrict__ hbuf, const T* __restrict__ kappa, 
     pbuf[(long long)y * G.nx + x] = -C.gamma * lap;
 }
 
-template <typename T>
-__global__ void k_pf_f(const T* __restrict__ f, const T* __restrict__ pbuf, T* p, T* fx, T* fy,
-                       Geom G, Consts<T> C)
+template <typename T, typename SM>
+__global__ void k_pf_f(Pops<T, SM> P, const T* __restrict__ pbuf, T* p, T* fx, T* fy, Geom G,
+                       Consts<T> C)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= G.nx) return;
     const int xm = wrapi(x - 1, G.nx), xp = wrapi(x + 1, G.nx);
     const int ym = wrapi(y - 1, G.ny), yp = wrapi(y + 1, G.ny);
-    auto P = [&](int yy, int xx) { return pbuf[(long long)yy * G.nx + xx]; };
-    const T gpx = (P(y, xp) - P(y, xm)) / T(3) + (P(yp, xp) - P(yp, xm) + P(ym, xp) - P(ym, xm)) / T(12);
-    const T gpy = (P(yp, x) - P(ym, x)) / T(3) + (P(yp, xp) - P(ym, xp) + P(yp, xm) - P(ym, xm)) / T(12);
+    auto Pp = [&](int yy, int xx) { return pbuf[(long long)yy * G.nx + xx]; };
+    const T gpx = (Pp(y, xp) - Pp(y, xm)) / T(3) + (Pp(yp, xp) - Pp(yp, xm) + Pp(ym, xp) - Pp(ym, xm)) / T(12);
+    const T gpy = (Pp(yp, x) - Pp(ym, x)) / T(3) + (Pp(yp, xp) - Pp(ym, xp) + Pp(yp, xm) - Pp(ym, xm)) / T(12);
     T v[9], hh, jx, jy;
-    pull_at(f, G, x, y, C.href, v);
+    pull_at(P, G, x, y, v);
     moments9(v, hh, jx, jy);
     const T fr = C.nu6 / (T(2) * hh * hh + T(6) * C.delta * hh + T(3) * C.delta * C.delta);
     const long long i = (long long)y * G.nx + x;
-    if (p) p[i] = P(y, x);
+    if (p) p[i] = Pp(y, x);
     if (fx) fx[i] = -hh * gpx - fr * jx + hh * C.gx;
     if (fy) fy[i] = -hh * gpy - fr * jy + hh * C.gy;
 }
@@ -181,18 +236,8 @@ __device__ __forceinline__ Comp warp_reduce(Comp a)
 
 constexpr int kMassThreads = 256;
 
-// Sum of every stored population (the total liquid volume: streaming only
-// permutes populations on the periodic lattice).  One (s, c) pair per block.
-template <typename T>
-__global__ void __launch_bounds__(kMassThreads) k_mass_partial(const T* __restrict__ f, Geom G,
-                                                               double* partials)
+__device__ __forceinline__ void block_store(Comp a, double* partials)
 {
-    Comp a{0.0, 0.0};
-    const long long nrows = 9LL * G.ny;
-    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
-        const T* p = f + row * G.pitch;  // plane l, row y: l * plane + y * pitch = row * pitch
-        for (int x = threadIdx.x; x < G.nx; x += blockDim.x) comp_add(a, (double)p[x]);
-    }
     a = warp_reduce(a);
     __shared__ Comp sm[kMassThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -208,6 +253,20 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(const T* __restri
     }
 }
 
+// Sum of every stored population, decoded (the total liquid volume minus
+// nx*ny*href: streaming only permutes populations on the periodic lattice).
+template <typename T, typename SM>
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial(Pops<T, SM> P, Geom G, double* partials)
+{
+    Comp a{0.0, 0.0};
+    const long long nrows = 9LL * G.ny;
+    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int l = (int)(row / G.ny), y = (int)(row % G.ny);
+        for (int x = threadIdx.x; x < G.nx; x += blockDim.x) comp_add(a, (double)P.raw(l, P.at(y, x)));
+    }
+    block_store(a, partials);
+}
+
 // Plain compensated sum of n values (used for the mean initial height).
 template <typename T>
 __global__ void __launch_bounds__(kMassThreads) k_sum_partial(const T* __restrict__ x, long long n,
@@ -217,19 +276,7 @@ __global__ void __launch_bounds__(kMassThreads) k_sum_partial(const T* __restric
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         comp_add(a, (double)x[i]);
-    a = warp_reduce(a);
-    __shared__ Comp sm[kMassThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sm[wid] = a;
-    __syncthreads();
-    if (wid == 0) {
-        Comp b = lane < kMassThreads / 32 ? sm[lane] : Comp{0.0, 0.0};
-        b = warp_reduce(b);
-        if (lane == 0) {
-            partials[2 * blockIdx.x] = b.s;
-            partials[2 * blockIdx.x + 1] = b.c;
-        }
-    }
+    block_store(a, partials);
 }
 
 __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* partials, int n, double* out)
@@ -251,15 +298,15 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* parti
     }
 }
 
-template <typename T>
-__global__ void k_check(const T* __restrict__ f, Geom G, T href, int* flag)
+template <typename T, typename SM>
+__global__ void k_check(Pops<T, SM> P, Geom G, int* flag)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     int bad = 0;
     if (x < G.nx) {
         T v[9], hh, jx, jy;
-        pull_at(f, G, x, y, href, v);
+        pull_at(P, G, x, y, v);
         for (int l = 0; l < 9; ++l)
             if (!isfinite((double)v[l])) bad |= 1;
         moments9(v, hh, jx, jy);
@@ -270,10 +317,11 @@ __global__ void k_check(const T* __restrict__ f, Geom G, T href, int* flag)
     if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, bad);
 }
 
-// State export in double: (f_0 - href) + href is exact in double for float
-// storage, so an export / import round trip reproduces the stored bits.
-template <typename T>
-__global__ void k_get_state(const T* __restrict__ f, double* out, Geom G, T href)
+// State export in double: decoded values plus href in double are exact for
+// float and 16-bit storage, so an export / import round trip reproduces the
+// stored bits.
+template <typename T, typename SM>
+__global__ void k_get_state(Pops<T, SM> P, double* out, Geom G)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -281,14 +329,13 @@ __global__ void k_get_state(const T* __restrict__ f, double* out, Geom G, T href
     const long long n = (long long)G.nx * G.ny, i = (long long)y * G.nx + x;
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-        const int xs = wrapi(x - kCx[l], G.nx), ys = wrapi(y - kCy[l], G.ny);
-        const double v = (double)f[l * G.plane + (long long)ys * G.pitch + xs];
-        out[l * n + i] = l == 0 ? v + (double)href : v;
+        const double v = (double)P.raw(l, P.at(wrapi(y - kCy[l], G.ny), wrapi(x - kCx[l], G.nx)));
+        out[l * n + i] = l == 0 ? v + (double)P.href : v;
     }
 }
 
-template <typename T>
-__global__ void k_set_state(T* f, const double* __restrict__ in, Geom G, T href)
+template <typename T, typename SM>
+__global__ void k_set_state(Pops<T, SM> P, const double* __restrict__ in, Geom G)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -298,11 +345,67 @@ __global__ void k_set_state(T* f, const double* __restrict__ in, Geom G, T href)
     for (int l = 0; l < 9; ++l) {
         const long long src = (long long)wrapi(y + kCy[l], G.ny) * G.nx + wrapi(x + kCx[l], G.nx);
         const double v = in[l * n + src];
-        f[l * G.plane + (long long)y * G.pitch + x] = T(l == 0 ? v - (double)href : v);
+        P.put(l, P.at(y, x), T(l == 0 ? v - (double)P.href : v));
     }
 }
 
 inline dim3 grid2d(const Geom& G, int bx) { return dim3((G.nx + bx - 1) / bx, G.ny); }
+
+template <typename T, typename SM>
+cudaError_t init_t(const StoreDesc& D, void* f, const void* h0, const Geom& G, double g, cudaStream_t st)
+{
+    k_init<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), (const T*)h0, G, T(g));
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t moments_t(const StoreDesc& D, const void* f, void* h, void* ux, void* uy, const Geom& G,
+                      cudaStream_t st)
+{
+    k_moments<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), (T*)h, (T*)ux, (T*)uy, G);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t pf_t(const StoreDesc& D, const void* f, const void* kappa, void* p, void* fx, void* fy,
+                 void* sh, void* sp, const Geom& G, const Consts<T>& C, cudaStream_t st)
+{
+    const auto P = make_pops<T, SM>(f, G, D);
+    k_pf_h<T, SM><<<grid2d(G, 128), 128, 0, st>>>(P, (T*)sh, G);
+    k_pf_p<T><<<grid2d(G, 128), 128, 0, st>>>((const T*)sh, (const T*)kappa, (T*)sp, G, C);
+    k_pf_f<T, SM><<<grid2d(G, 128), 128, 0, st>>>(P, (const T*)sp, (T*)p, (T*)fx, (T*)fy, G, C);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t mass_t(const StoreDesc& D, const void* f, const Geom& G, double* partials, int nblocks,
+                   double* result, cudaStream_t st)
+{
+    k_mass_partial<T, SM><<<nblocks, kMassThreads, 0, st>>>(make_pops<T, SM>(f, G, D), G, partials);
+    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t check_t(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st)
+{
+    k_check<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), G, flag);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t get_t(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st)
+{
+    k_get_state<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), out, G);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t set_t(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st)
+{
+    k_set_state<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), in, G);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -312,70 +415,79 @@ int mass_blocks(const Geom& G)
     return (int)(rows < 1184 ? rows : 1184);
 }
 
-#define TFLBM_AUX_DEF(T, SUF)                                                                   \
-    cudaError_t launch_kappa_##SUF(T* kappa, const T* theta, int nx, int ny, int ne, int me,   \
-                                   double hstar, cudaStream_t st)                              \
-    {                                                                                           \
-        long long n = (long long)nx * ny;                                                       \
-        int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);                    \
-        k_kappa<T><<<blocks, 256, 0, st>>>(kappa, theta, n, ne, me, hstar);                     \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_init_##SUF(T* f, const T* h0, const Geom& G, T g, T href,              \
-                                  cudaStream_t st)                                             \
-    {                                                                                           \
-        k_init<T><<<grid2d(G, 128), 128, 0, st>>>(f, h0, G, g, href);                           \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_moments_##SUF(const T* f, T* h, T* ux, T* uy, const Geom& G,             \
-                                     T href, cudaStream_t st)                                  \
-    {                                                                                           \
-        k_moments<T><<<grid2d(G, 128), 128, 0, st>>>(f, h, ux, uy, G, href);                    \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_sum_##SUF(const T* x, long long n, double* partials, int nblocks,        \
-                                 double* result, cudaStream_t st)                              \
-    {                                                                                           \
-        k_sum_partial<T><<<nblocks, kMassThreads, 0, st>>>(x, n, partials);                     \
-        k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);                    \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_pressure_force_##SUF(const T* f, const T* kappa, T* p, T* fx, T* fy,     \
-                                            T* sh, T* sp, const Geom& G, const Consts<T>& C,    \
-                                            cudaStream_t st)                                   \
-    {                                                                                           \
-        k_pf_h<T><<<grid2d(G, 128), 128, 0, st>>>(f, sh, G, C);                                 \
-        k_pf_p<T><<<grid2d(G, 128), 128, 0, st>>>(sh, kappa, sp, G, C);                         \
-        k_pf_f<T><<<grid2d(G, 128), 128, 0, st>>>(f, sp, p, fx, fy, G, C);                      \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_mass_##SUF(const T* f, const Geom& G, double* partials, int nblocks,     \
-                                  double* result, cudaStream_t st)                             \
-    {                                                                                           \
-        k_mass_partial<T><<<nblocks, kMassThreads, 0, st>>>(f, G, partials);                    \
-        k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);                    \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_check_##SUF(const T* f, const Geom& G, T href, int* flag,               \
-                                   cudaStream_t st)                                            \
-    {                                                                                           \
-        k_check<T><<<grid2d(G, 128), 128, 0, st>>>(f, G, href, flag);                           \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_get_state_##SUF(const T* f, double* out, const Geom& G, T href,         \
-                                       cudaStream_t st)                                        \
-    {                                                                                           \
-        k_get_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, out, G, href);                        \
-        return cudaGetLastError();                                                              \
-    }                                                                                           \
-    cudaError_t launch_set_state_##SUF(T* f, const double* in, const Geom& G, T href,          \
-                                       cudaStream_t st)                                        \
-    {                                                                                           \
-        k_set_state<T><<<grid2d(G, 128), 128, 0, st>>>(f, in, G, href);                         \
-        return cudaGetLastError();                                                              \
+// Dispatch over the storage type: F32 and the 16-bit stores compute in float,
+// F64 in double.
+#define TFLBM_DISPATCH(D, CALL)                                                      \
+    switch ((D).store) {                                                             \
+        case kStoreF32: { using T = float; using SM = float; return CALL; }          \
+        case kStoreF64: { using T = double; using SM = double; return CALL; }        \
+        case kStoreF16: { using T = float; using SM = __half; return CALL; }         \
+        case kStoreBF16: { using T = float; using SM = __nv_bfloat16; return CALL; } \
+        default: return cudaErrorInvalidValue;                                       \
     }
 
-TFLBM_AUX_DEF(float, f32)
-TFLBM_AUX_DEF(double, f64)
+cudaError_t aux_init(const StoreDesc& D, void* f, const void* h0, const Geom& G, double g, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (init_t<T, SM>(D, f, h0, G, g, st)))
+}
+
+cudaError_t aux_moments(const StoreDesc& D, const void* f, void* h, void* ux, void* uy, const Geom& G,
+                        cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (moments_t<T, SM>(D, f, h, ux, uy, G, st)))
+}
+
+cudaError_t aux_pressure_force(const StoreDesc& D, const void* f, const void* kappa, void* p, void* fx,
+                               void* fy, void* sh, void* sp, const Geom& G, const Consts<float>* C32,
+                               const Consts<double>* C64, cudaStream_t st)
+{
+    switch (D.store) {
+        case kStoreF32: return pf_t<float, float>(D, f, kappa, p, fx, fy, sh, sp, G, *C32, st);
+        case kStoreF64: return pf_t<double, double>(D, f, kappa, p, fx, fy, sh, sp, G, *C64, st);
+        case kStoreF16: return pf_t<float, __half>(D, f, kappa, p, fx, fy, sh, sp, G, *C32, st);
+        case kStoreBF16: return pf_t<float, __nv_bfloat16>(D, f, kappa, p, fx, fy, sh, sp, G, *C32, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t aux_mass(const StoreDesc& D, const void* f, const Geom& G, double* partials, int nblocks,
+                     double* result, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (mass_t<T, SM>(D, f, G, partials, nblocks, result, st)))
+}
+
+cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (check_t<T, SM>(D, f, G, flag, st)))
+}
+
+cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (get_t<T, SM>(D, f, out, G, st)))
+}
+
+cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (set_t<T, SM>(D, f, in, G, st)))
+}
+
+cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
+                      double hstar, cudaStream_t st)
+{
+    const long long n = (long long)nx * ny;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (dbl) k_kappa<double><<<blocks, 256, 0, st>>>((double*)kappa, (const double*)theta, n, ne, me, hstar);
+    else k_kappa<float><<<blocks, 256, 0, st>>>((float*)kappa, (const float*)theta, n, ne, me, hstar);
+    return cudaGetLastError();
+}
+
+cudaError_t aux_sum(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
+                    cudaStream_t st)
+{
+    if (dbl) k_sum_partial<double><<<nblocks, kMassThreads, 0, st>>>((const double*)x, n, partials);
+    else k_sum_partial<float><<<nblocks, kMassThreads, 0, st>>>((const float*)x, n, partials);
+    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
 
 }  // namespace tflbm

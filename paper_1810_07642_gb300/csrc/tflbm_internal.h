@@ -26,6 +26,9 @@ struct Consts {
     T kappa_u;    // uniform kappa (used when no kappa field)
     T pi_sgn;     // +1 or -1
     T href;       // reference height: the rest population is stored as f_0 - href
+    // 16-bit storage of the moving populations: q = (f_l - R_l) * mscale,
+    // R_l = f_eq_l(href, 0) = r_axis (odd l) or r_diag (even l); minv = 1/mscale
+    T mscale, minv, r_axis, r_diag;
     int n_exp, m_exp;
 };
 
@@ -35,51 +38,51 @@ struct Shape {
     int rows;     // rows per CTA
 };
 
-// fin: post-collision populations of step t (pre-streaming);
-// fout: post-collision populations of step t + 1.  kappa: [ny][nx] or null.
-cudaError_t launch_step_f32(const float* fin, float* fout, const float* kappa,
-                            const Geom& G, const Consts<float>& C, const Shape& S,
-                            cudaStream_t st);
-cudaError_t launch_step_f64(const double* fin, double* fout, const double* kappa,
-                            const Geom& G, const Consts<double>& C, const Shape& S,
-                            cudaStream_t st);
+// Storage of the 8 moving populations.
+enum Store { kStoreF32 = 0, kStoreF64 = 1, kStoreF16 = 2, kStoreBF16 = 3 };
 
-// Storage convention: plane 0 holds f_0 - href, planes 1..8 hold f_l.  In
+// fin: post-collision populations of step t (pre-streaming); fout: those of
+// step t + 1.  A population buffer holds plane 0 (f_0 - href, compute type)
+// followed by the 8 moving planes in the storage type, each `plane` elements.
+// kappa: [ny][nx] or null.
+cudaError_t launch_step(int store, const void* fin, void* fout, const void* kappa, const Geom& G,
+                        const Consts<float>* C32, const Consts<double>* C64, const Shape& S,
+                        cudaStream_t st);
+// Resident CTAs per SM of the step kernel for a launch shape (0 if unknown).
+int step_blocks_per_sm(int store, int block_x, bool omega1, bool kfield);
+
+// Storage convention: plane 0 holds f_0 - href, planes 1..8 hold f_l (or its
+// 16-bit encoding, see Consts).  In
 // this model the rest population carries almost all of h (f_0 ~ h, the moving
 // populations are O(g h^2, h u)), so storing its deviation from a per-run
 // reference height keeps rounding errors proportional to the perturbation
 // rather than to h and removes the systematic mass drift of near-flat films.
 
-// Resident CTAs per SM of the step kernel for a launch shape (0 if unknown).
-int step_blocks_per_sm_f32(int block_x, bool omega1, bool kfield);
-int step_blocks_per_sm_f64(int block_x, bool omega1, bool kfield);
+// Storage of one handle, as the auxiliary kernels need it (values in double;
+// each kernel casts them to its compute type).
+struct StoreDesc {
+    int store;
+    double href, mscale, minv, r_axis, r_diag;
+};
 
-// Auxiliary kernels, one set per storage type.
-#define TFLBM_AUX_DECL(T, SUF)                                                             \
-    cudaError_t launch_kappa_##SUF(T* kappa, const T* theta, int nx, int ny,               \
-                                   int n_exp, int m_exp, double hstar, cudaStream_t st);   \
-    cudaError_t launch_init_##SUF(T* f, const T* h0, const Geom& G, T g, T href,           \
-                                  cudaStream_t st);                                      \
-    cudaError_t launch_moments_##SUF(const T* f, T* h, T* ux, T* uy, const Geom& G,        \
-                                     T href, cudaStream_t st);                            \
-    cudaError_t launch_sum_##SUF(const T* x, long long n, double* partials, int nblocks,   \
-                                 double* result, cudaStream_t st);                        \
-    cudaError_t launch_pressure_force_##SUF(const T* f, const T* kappa, T* p, T* fx,       \
-                                            T* fy, T* scratch_h, T* scratch_p,            \
-                                            const Geom& G, const Consts<T>& C,            \
-                                            cudaStream_t st);                             \
-    cudaError_t launch_mass_##SUF(const T* f, const Geom& G, double* partials,             \
-                                  int nblocks, double* result, cudaStream_t st);           \
-    cudaError_t launch_check_##SUF(const T* f, const Geom& G, T href, int* flag,           \
-                                   cudaStream_t st);                                      \
-    cudaError_t launch_get_state_##SUF(const T* f, double* out, const Geom& G, T href,     \
-                                       cudaStream_t st);                                  \
-    cudaError_t launch_set_state_##SUF(T* f, const double* in, const Geom& G, T href,      \
-                                       cudaStream_t st);
-
-TFLBM_AUX_DECL(float, f32)
-TFLBM_AUX_DECL(double, f64)
-#undef TFLBM_AUX_DECL
+// Auxiliary kernels, dispatched over the storage type.  Field buffers (h0,
+// theta, kappa, moments, p, F, scratch) are in the compute type: double for
+// kStoreF64, float otherwise.
+cudaError_t aux_init(const StoreDesc& D, void* f, const void* h0, const Geom& G, double g, cudaStream_t st);
+cudaError_t aux_moments(const StoreDesc& D, const void* f, void* h, void* ux, void* uy, const Geom& G,
+                        cudaStream_t st);
+cudaError_t aux_pressure_force(const StoreDesc& D, const void* f, const void* kappa, void* p, void* fx,
+                               void* fy, void* sh, void* sp, const Geom& G, const Consts<float>* C32,
+                               const Consts<double>* C64, cudaStream_t st);
+cudaError_t aux_mass(const StoreDesc& D, const void* f, const Geom& G, double* partials, int nblocks,
+                     double* result, cudaStream_t st);
+cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st);
+cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st);
+cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st);
+cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
+                      double hstar, cudaStream_t st);
+cudaError_t aux_sum(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
+                    cudaStream_t st);
 
 // Number of partial sums the mass reduction writes (its grid size), and the
 // number the plain field sum writes.

@@ -28,6 +28,9 @@
 //    are returned to the opposite pair (1, 5), so in FP32 the collision
 //    conserves local mass up to roundings of the small moving populations.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "tflbm_internal.h"
@@ -69,6 +72,27 @@ __device__ __forceinline__ T fdisj(T r, int n, int m)
 
 template <typename S> __device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
 
+// Element conversions of the moving-population storage types.
+__device__ __forceinline__ float to_f(float q) { return q; }
+__device__ __forceinline__ double to_f(double q) { return q; }
+__device__ __forceinline__ float to_f(__half q) { return __half2float(q); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 q) { return __bfloat162float(q); }
+template <typename SM> __device__ __forceinline__ SM from_f(float v);
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// A moving population l (1..8) is kept as is when its storage type is the
+// compute type.  In 16-bit storage it is kept as q = (f_l - R_l) * scale,
+// R_l = f_eq_l(href, u = 0) (gh^2/6 on the axes, gh^2/24 on the diagonals),
+// and read back as q / scale + R_l: one fma with an exact product, so the
+// writer can compute the bits every reader will see.
+template <typename SM, typename T>
+__device__ __forceinline__ T load_moving(SM q, int l, const Consts<T>& C)
+{
+    if constexpr (std::is_same<SM, T>::value) return q;
+    else return fmaf(to_f(q), C.minv, (l & 1) ? C.r_axis : C.r_diag);
+}
+
 // Error-free sum (Knuth's TwoSum): a + b = s + e exactly.  The _rn
 // intrinsics keep the compiler from contracting or reordering the steps.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
@@ -86,23 +110,25 @@ __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e
 
 // Pull the nine populations arriving at column x of row y: i0 = y*pitch + x,
 // im / ip the same row offset for the wrapped columns x-1 / x+1, dm / dp the
-// row steps to rows y-1 / y+1 (wrapped, in elements).  32-bit offsets: the
+// row steps to rows y-1 / y+1 (wrapped, in elements).  Plane 0 (f_0 - href)
+// is f0[i]; moving population l is fm[(l-1)*plane + i].  32-bit offsets: the
 // host checks 9 * plane < 2^31.  Order of Eq. (speeds): 1 (1,0) 2 (1,1)
 // 3 (0,1) 4 (-1,1) 5 (-1,0) 6 (-1,-1) 7 (0,-1) 8 (1,-1); population l at x
 // comes from x - c_l.
-template <typename S, typename T>
-__device__ __forceinline__ void pull9(const S* __restrict__ f, int plane, int i0, int im, int ip,
-                                      int dm, int dp, T (&v)[9])
+template <typename SM, typename T>
+__device__ __forceinline__ void pull9(const T* __restrict__ f0, const SM* __restrict__ fm,
+                                      int plane, int i0, int im, int ip, int dm, int dp,
+                                      const Consts<T>& C, T (&v)[9])
 {
-    v[0] = T(ldro(f + i0));
-    v[1] = T(ldro(f + (plane + im)));
-    v[2] = T(ldro(f + (2 * plane + im + dm)));
-    v[3] = T(ldro(f + (3 * plane + i0 + dm)));
-    v[4] = T(ldro(f + (4 * plane + ip + dm)));
-    v[5] = T(ldro(f + (5 * plane + ip)));
-    v[6] = T(ldro(f + (6 * plane + ip + dp)));
-    v[7] = T(ldro(f + (7 * plane + i0 + dp)));
-    v[8] = T(ldro(f + (8 * plane + im + dp)));
+    v[0] = ldro(f0 + i0);
+    v[1] = load_moving(ldro(fm + im), 1, C);
+    v[2] = load_moving(ldro(fm + (plane + im + dm)), 2, C);
+    v[3] = load_moving(ldro(fm + (2 * plane + i0 + dm)), 3, C);
+    v[4] = load_moving(ldro(fm + (3 * plane + ip + dm)), 4, C);
+    v[5] = load_moving(ldro(fm + (4 * plane + ip)), 5, C);
+    v[6] = load_moving(ldro(fm + (5 * plane + ip + dp)), 6, C);
+    v[7] = load_moving(ldro(fm + (6 * plane + i0 + dp)), 7, C);
+    v[8] = load_moving(ldro(fm + (7 * plane + im + dp)), 8, C);
 }
 
 // dh = sum_l v_l with v_0 = f_0 - href: the moving populations are summed
@@ -132,11 +158,12 @@ __device__ __forceinline__ T film_pressure(const T* hn, const T* hc, const T* hs
     return -C.gamma * lap;
 }
 
-template <typename S, typename T, int BX, bool OMEGA1, bool KFIELD>
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
 __global__ void __launch_bounds__(BX, OMEGA1 ? 1024 / BX : 1)
-k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ kappa,
-       const Geom G, const Consts<T> C)
+k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
+       SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
+    constexpr bool NARROW = !std::is_same<SM, T>::value;  // 16-bit moving populations
     constexpr int W = BX - 4;     // output columns per CTA
     __shared__ T hsm[4][BX];      // h - href ring: slot t = column x0 - 2 + t
     __shared__ T psm[4][BX];      // p ring, same columns
@@ -186,7 +213,7 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
     auto pull_row = [&](int wb, int w, int wa) {
         const int r0 = w * pitch;
         const int below = (dir > 0 ? wb : wa) - w, above = (dir > 0 ? wa : wb) - w;
-        pull9<S, T>(fin, plane, r0 + x, r0 + xm, r0 + xp, below * pitch, above * pitch, v);
+        pull9<SM, T>(fin0, finm, plane, r0 + x, r0 + xm, r0 + xp, below * pitch, above * pitch, C, v);
     };
     // prologue: loads of the first h row r(0) and kappa of row r(-1)
     if (hcol) pull_row(wm1, w0, w1);
@@ -271,27 +298,48 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
                 o4 = one_m_omega * f[4] + w * (Sb + Db) + Qb;
                 o8 = one_m_omega * f[8] + w * (Sb - Db) - Qb;
             }
-            // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l;
-            // the exact rounding residuals of the pull sum and of this
-            // subtraction go to the opposite pair (1, 5), half each, so the
-            // stored populations sum to the pulled ones (mass conserved to
-            // roundings of small values) and the momentum is untouched.
+            // In 16-bit storage, round the moving populations to what the
+            // readers will reconstruct before the rest population is formed.
+            SM q1, q2, q3, q4, q5, q6, q7, q8;
+            if constexpr (NARROW) {
+                auto narrow = [&](T& o, SM& q, T R) {
+                    q = from_f<SM>((o - R) * C.mscale);
+                    o = fmaf(to_f(q), C.minv, R);
+                };
+                narrow(o1, q1, C.r_axis); narrow(o3, q3, C.r_axis);
+                narrow(o5, q5, C.r_axis); narrow(o7, q7, C.r_axis);
+                narrow(o2, q2, C.r_diag); narrow(o4, q4, C.r_diag);
+                narrow(o6, q6, C.r_diag); narrow(o8, q8, C.r_diag);
+            }
+            // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l.
+            // The error-free sums give the exact rounding residuals of the
+            // pull sum and of this subtraction.  With full-width storage they
+            // go to the opposite pair (1, 5), half each, so the stored
+            // populations sum to the pulled ones (mass conserved to roundings
+            // of small values) and the momentum is untouched; with 16-bit
+            // storage they are added to the rest population itself.
             const T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
             T o0v, e2;
             two_sum(dh, -osum, o0v, e2);
-            const T half_r = (erv[s3] + e2) * T(0.5);
-            o1 += half_r;
-            o5 += half_r;
-            S* out = fout + (o * pitch + x);
-            out[0] = S(o0v);
-            out[plane] = S(o1);
-            out[2 * plane] = S(o2);
-            out[3 * plane] = S(o3);
-            out[4 * plane] = S(o4);
-            out[5 * plane] = S(o5);
-            out[6 * plane] = S(o6);
-            out[7 * plane] = S(o7);
-            out[8 * plane] = S(o8);
+            if constexpr (NARROW) {
+                o0v += erv[s3] + e2;
+            } else {
+                const T half_r = (erv[s3] + e2) * T(0.5);
+                o1 += half_r;
+                o5 += half_r;
+                q1 = o1; q2 = o2; q3 = o3; q4 = o4; q5 = o5; q6 = o6; q7 = o7; q8 = o8;
+            }
+            const int io = o * pitch + x;
+            fout0[io] = o0v;
+            SM* om = foutm + io;
+            om[0] = q1;
+            om[plane] = q2;
+            om[2 * plane] = q3;
+            om[3 * plane] = q4;
+            om[4 * plane] = q5;
+            om[5 * plane] = q6;
+            om[6 * plane] = q7;
+            om[7 * plane] = q8;
         }
         // advance the wrapped row window
         wm1 = w0;
@@ -314,34 +362,34 @@ k_step(const S* __restrict__ fin, S* __restrict__ fout, const T* __restrict__ ka
     }
 }
 
-template <typename S, typename T, int BX>
-cudaError_t launch_step_bx(const S* fin, S* fout, const T* kappa, const Geom& G,
-                           const Consts<T>& C, int rows, cudaStream_t st)
+template <typename SM, typename T, int BX>
+cudaError_t launch_step_bx(const T* fin0, const SM* finm, T* fout0, SM* foutm, const T* kappa,
+                           const Geom& G, const Consts<T>& C, int rows, cudaStream_t st)
 {
     int bands = (G.ny + rows - 1) / rows;
     if (bands > 65535) bands = 65535;
     dim3 grid((G.nx + BX - 5) / (BX - 4), bands);
     const bool om1 = (C.omega == T(1));
     if (kappa) {
-        if (om1) k_step<S, T, BX, true, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
-        else k_step<S, T, BX, false, true><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
+        if (om1) k_step<SM, T, BX, true, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+        else k_step<SM, T, BX, false, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
     } else {
-        if (om1) k_step<S, T, BX, true, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
-        else k_step<S, T, BX, false, false><<<grid, BX, 0, st>>>(fin, fout, kappa, G, C);
+        if (om1) k_step<SM, T, BX, true, false><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+        else k_step<SM, T, BX, false, false><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
     }
     return cudaGetLastError();
 }
 
 // Resident CTAs per SM of one instantiation (for sizing the grid).
-template <typename S, typename T, int BX>
+template <typename SM, typename T, int BX>
 int blocks_per_sm_bx(bool omega1, bool kfield)
 {
     int n = 0;
     cudaError_t e;
-    if (kfield) e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, true, true>, BX, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, false, true>, BX, 0);
-    else e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, true, false>, BX, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<S, T, BX, false, false>, BX, 0);
+    if (kfield) e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, true, true>, BX, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, false, true>, BX, 0);
+    else e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, true, false>, BX, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, false, false>, BX, 0);
     return e == cudaSuccess ? n : 0;
 }
 

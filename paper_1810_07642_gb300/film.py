@@ -11,7 +11,9 @@ import torch
 
 from . import _lib as L
 
-_DT = {"f32": (L.TF_LBM_F32, torch.float32), "f64": (L.TF_LBM_F64, torch.float64)}
+# storage name -> (library dtype code, torch dtype of fields and inputs)
+_DT = {"f32": (L.TF_LBM_F32, torch.float32), "f64": (L.TF_LBM_F64, torch.float64),
+       "f16": (L.TF_LBM_F16, torch.float32), "bf16": (L.TF_LBM_BF16, torch.float32)}
 
 
 def make_params(nx, ny, dtype="f32", tau=1.0, gamma=0.01, g=0.0, delta=1.0, hstar=0.07,
