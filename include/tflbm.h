@@ -81,7 +81,9 @@ enum {
 /* bits of the status word returned by tf_lbm_check */
 enum {
     TF_LBM_STATUS_NONFINITE = 1,  /* some population or h is NaN or inf */
-    TF_LBM_STATUS_NONPOSITIVE = 2 /* some h <= 0 (Pi and alpha singular) */
+    TF_LBM_STATUS_NONPOSITIVE = 2, /* some h <= 0 (Pi and alpha singular) */
+    TF_LBM_STATUS_TIMEOUT = 4      /* a step kernel gave up waiting for its
+                                      own bulk copies (results invalid)    */
 };
 
 /* Physical and numerical parameters (lattice units, dx = dt = 1). */
@@ -103,15 +105,19 @@ typedef struct tf_lbm_params {
 typedef struct tf_lbm_handle tf_lbm_handle;
 
 /* Kernel launch shape of the fused step (for autotuning).
- *   block_x: CTA width in lattice columns (32, 64, 128 or 256);
+ *   block_x: CTA width in lattice columns (64, 128 or 256);
  *   rows:    lattice rows marched by one CTA (>= 1);
  *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
- *            otherwise an even number >= 2). */
+ *            otherwise an even number >= 2);
+ *   pipeline: 1 = every thread loads its own populations, one row ahead
+ *            (default); 0 = row segments streamed into shared memory by
+ *            bulk copies four rows ahead (needs nx a multiple of 8, >= 16).
+ * Results do not depend on rows, graph_chunk or pipeline. */
 typedef struct tf_lbm_launch {
     int32_t block_x;
     int32_t rows;
     int32_t graph_chunk;
-    int32_t reserved;
+    int32_t pipeline;
 } tf_lbm_launch;
 
 /* Create a simulation and set f_l(x, 0) = f_eq_l(h0(x), u = 0).
@@ -147,7 +153,8 @@ int tf_lbm_pressure_force(tf_lbm_handle* H, void* p, void* fx, void* fy, void* s
 int tf_lbm_mass(tf_lbm_handle* H, double* mass_host, void* stream);
 
 /* Scan the current state: *status_host = OR of TF_LBM_STATUS_* bits (0 when
- * every population and h is finite and every h > 0).  Synchronises `stream`. */
+ * every population and h is finite and every h > 0 and no step kernel timed
+ * out).  Synchronises `stream`. */
 int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream);
 
 /* Copy the post-streaming populations f_l(x, t) out to / in from a device

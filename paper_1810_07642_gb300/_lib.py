@@ -15,7 +15,7 @@ TF_LBM_F32, TF_LBM_F64, TF_LBM_F16, TF_LBM_BF16 = 0, 1, 2, 3
 TF_LBM_OK = 0
 TF_LBM_ERR_ARG, TF_LBM_ERR_CUDA, TF_LBM_ERR_NOMEM = -1, -2, -3
 TF_LBM_ERR_NONFINITE, TF_LBM_ERR_UNSUPPORTED = -4, -5
-TF_LBM_STATUS_NONFINITE, TF_LBM_STATUS_NONPOSITIVE = 1, 2
+TF_LBM_STATUS_NONFINITE, TF_LBM_STATUS_NONPOSITIVE, TF_LBM_STATUS_TIMEOUT = 1, 2, 4
 
 EXPORTED = [
     "tf_lbm_init", "tf_lbm_step", "tf_lbm_moments", "tf_lbm_pressure_force", "tf_lbm_mass",
@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
 class Launch(ctypes.Structure):
     """Mirror of tf_lbm_launch."""
     _fields_ = [("block_x", ctypes.c_int32), ("rows", ctypes.c_int32),
-                ("graph_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_chunk", ctypes.c_int32), ("pipeline", ctypes.c_int32)]
 
 
 _lib = None
@@ -151,8 +151,9 @@ def tf_lbm_get_launch(handle: int) -> Launch:
     return out
 
 
-def tf_lbm_set_launch(handle: int, block_x: int, rows: int, graph_chunk: int) -> None:
-    L = Launch(block_x, rows, graph_chunk, 0)
+def tf_lbm_set_launch(handle: int, block_x: int, rows: int, graph_chunk: int,
+                      pipeline: int = 0) -> None:
+    L = Launch(block_x, rows, graph_chunk, pipeline)
     _check(lib().tf_lbm_set_launch(_VP(handle), ctypes.byref(L)), _VP(handle))
 
 

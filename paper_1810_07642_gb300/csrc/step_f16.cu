@@ -14,9 +14,9 @@ static cudaError_t launch_n(const void* fin, void* fout, const void* kappa, cons
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
     const float* k = (const float*)kappa;
     switch (S.block_x) {
-        case 64: return launch_step_bx<SM, float, 64>(f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 128: return launch_step_bx<SM, float, 128>(f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 256: return launch_step_bx<SM, float, 256>(f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 64: return launch_step_bx<SM, float, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 128: return launch_step_bx<SM, float, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 256: return launch_step_bx<SM, float, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -31,20 +31,20 @@ cudaError_t launch_step_narrow(int store, const void* fin, void* fout, const voi
 }
 
 template <typename SM>
-static int bps(int block_x, bool omega1, bool kfield)
+static int bps(int pipeline, int block_x, bool omega1, bool kfield)
 {
     switch (block_x) {
-        case 64: return blocks_per_sm_bx<SM, float, 64>(omega1, kfield);
-        case 128: return blocks_per_sm_bx<SM, float, 128>(omega1, kfield);
-        case 256: return blocks_per_sm_bx<SM, float, 256>(omega1, kfield);
+        case 64: return blocks_per_sm_bx<SM, float, 64>(pipeline, omega1, kfield);
+        case 128: return blocks_per_sm_bx<SM, float, 128>(pipeline, omega1, kfield);
+        case 256: return blocks_per_sm_bx<SM, float, 256>(pipeline, omega1, kfield);
         default: return 0;
     }
 }
 
-int blocks_per_sm_narrow(int store, int block_x, bool omega1, bool kfield)
+int blocks_per_sm_narrow(int store, int pipeline, int block_x, bool omega1, bool kfield)
 {
-    if (store == kStoreF16) return bps<__half>(block_x, omega1, kfield);
-    if (store == kStoreBF16) return bps<__nv_bfloat16>(block_x, omega1, kfield);
+    if (store == kStoreF16) return bps<__half>(pipeline, block_x, omega1, kfield);
+    if (store == kStoreBF16) return bps<__nv_bfloat16>(pipeline, block_x, omega1, kfield);
     return 0;
 }
 

@@ -7,7 +7,7 @@ namespace tflbm {
 cudaError_t launch_step_narrow(int store, const void* fin, void* fout, const void* kappa,
                                const Geom& G, const Consts<float>& C, const Shape& S,
                                cudaStream_t st);
-int blocks_per_sm_narrow(int store, int block_x, bool omega1, bool kfield);
+int blocks_per_sm_narrow(int store, int pipeline, int block_x, bool omega1, bool kfield);
 
 template <typename SM, typename T>
 static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, const Geom& G,
@@ -19,9 +19,9 @@ static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, 
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
     const T* k = (const T*)kappa;
     switch (S.block_x) {
-        case 64: return launch_step_bx<SM, T, 64>(f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 128: return launch_step_bx<SM, T, 128>(f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 256: return launch_step_bx<SM, T, 256>(f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 64: return launch_step_bx<SM, T, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 128: return launch_step_bx<SM, T, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 256: return launch_step_bx<SM, T, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -37,21 +37,21 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
     }
 }
 
-int step_blocks_per_sm(int store, int block_x, bool omega1, bool kfield)
+int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield)
 {
     if (store == kStoreF32 || store == kStoreF64) {
         const bool f = store == kStoreF32;
         switch (block_x) {
-            case 64: return f ? blocks_per_sm_bx<float, float, 64>(omega1, kfield)
-                              : blocks_per_sm_bx<double, double, 64>(omega1, kfield);
-            case 128: return f ? blocks_per_sm_bx<float, float, 128>(omega1, kfield)
-                               : blocks_per_sm_bx<double, double, 128>(omega1, kfield);
-            case 256: return f ? blocks_per_sm_bx<float, float, 256>(omega1, kfield)
-                               : blocks_per_sm_bx<double, double, 256>(omega1, kfield);
+            case 64: return f ? blocks_per_sm_bx<float, float, 64>(pipeline, omega1, kfield)
+                              : blocks_per_sm_bx<double, double, 64>(pipeline, omega1, kfield);
+            case 128: return f ? blocks_per_sm_bx<float, float, 128>(pipeline, omega1, kfield)
+                               : blocks_per_sm_bx<double, double, 128>(pipeline, omega1, kfield);
+            case 256: return f ? blocks_per_sm_bx<float, float, 256>(pipeline, omega1, kfield)
+                               : blocks_per_sm_bx<double, double, 256>(pipeline, omega1, kfield);
             default: return 0;
         }
     }
-    return blocks_per_sm_narrow(store, block_x, omega1, kfield);
+    return blocks_per_sm_narrow(store, pipeline, block_x, omega1, kfield);
 }
 
 }  // namespace tflbm

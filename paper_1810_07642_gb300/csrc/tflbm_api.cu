@@ -31,9 +31,10 @@ struct tf_lbm_handle {
     double* result = nullptr;
     int nmass = 0;
     int* flag = nullptr;
+    int* status = nullptr;     // device word kernels set (kStatusTimeout)
     void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
     int64_t time = 0;
-    Shape shape{128, 64};
+    Shape shape{128, 64, kPipeTma};
     int graph_chunk = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -107,6 +108,7 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.r_diag = T(H->desc.r_diag);
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
+    C.status = H->status;
     return C;
 }
 
@@ -177,7 +179,11 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool om1 = p.tau == 1.0;
-    int occ = step_blocks_per_sm(store_of(p.dtype), s.block_x, om1, kfield);
+    // per-thread loads: measured faster than the bulk-copy pipeline on GB300
+    // for this kernel, which is instruction-issue bound rather than latency
+    // bound once loads are prefetched a row ahead
+    s.pipeline = kPipeLdg;
+    int occ = step_blocks_per_sm(store_of(p.dtype), s.pipeline, s.block_x, om1, kfield);
     if (occ < 1) occ = 4;
     int bands = occ * sms / strips;
     if (bands < 1) bands = 1;
@@ -194,6 +200,8 @@ namespace tflbm {
 // Message for tf_lbm_last_error(NULL) from entry points without a handle.
 void set_thread_error(const std::string& msg) { g_init_err = msg; }
 }  // namespace tflbm
+
+static_assert(kStatusTimeout == TF_LBM_STATUS_TIMEOUT, "status bits out of sync");
 
 extern "C" {
 
@@ -252,7 +260,9 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     if ((e = cudaMalloc(&H->partials, sizeof(double) * 2 * H->nmass + sizeof(double))) != cudaSuccess)
         return bail(cuda_fail(H, e, "cudaMalloc scratch"));
     H->result = H->partials + 2 * H->nmass;
-    if ((e = cudaMalloc(&H->flag, sizeof(int))) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc flag"));
+    if ((e = cudaMalloc(&H->flag, 2 * sizeof(int))) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMalloc flag"));
+    H->status = H->flag + 1;
+    if ((e = cudaMemsetAsync(H->flag, 0, 2 * sizeof(int), st)) != cudaSuccess) return bail(cuda_fail(H, e, "cudaMemsetAsync"));
 
     const double kscale = (double)(params->n_exp - 1) * (params->m_exp - 1) /
                           ((double)(params->n_exp - params->m_exp) * params->hstar);
@@ -381,10 +391,10 @@ int tf_lbm_check(tf_lbm_handle* H, int32_t* status_host, void* stream)
     CK(H, cudaMemsetAsync(H->flag, 0, sizeof(int), st), "cudaMemsetAsync");
     cudaError_t e = aux_check(H->desc, H->buf[H->cur], H->G, H->flag, st);
     CK(H, e, "check kernel");
-    int v = 0;
-    CK(H, cudaMemcpyAsync(&v, H->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    int v[2] = {0, 0};
+    CK(H, cudaMemcpyAsync(v, H->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     CK(H, cudaStreamSynchronize(st), "cudaStreamSynchronize");
-    *status_host = v;
+    *status_host = v[0] | v[1];
     return TF_LBM_OK;
 }
 
@@ -418,7 +428,7 @@ int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out)
     out->block_x = H->shape.block_x;
     out->rows = H->shape.rows;
     out->graph_chunk = H->graph_chunk;
-    out->reserved = 0;
+    out->pipeline = H->shape.pipeline;
     return TF_LBM_OK;
 }
 
@@ -431,7 +441,12 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     if (in->rows < 1 || in->rows > 65535) return fail(H, TF_LBM_ERR_ARG, "rows must be in [1, 65535]");
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
+    if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg)
+        return fail(H, TF_LBM_ERR_ARG, "pipeline must be 0 (bulk copies) or 1 (per-thread loads)");
+    if (in->pipeline == kPipeTma && !tma_pipeline_ok(H->G.nx))
+        return fail(H, TF_LBM_ERR_ARG, "the bulk-copy pipeline needs nx to be a multiple of 8 and >= 16");
     drop_graphs(H);
+    H->shape.pipeline = in->pipeline;
     H->shape.block_x = bx;
     H->shape.rows = in->rows;
     H->graph_chunk = in->graph_chunk;

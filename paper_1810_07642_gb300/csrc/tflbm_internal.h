@@ -13,6 +13,15 @@ struct Geom {
     long long plane;  // ny * pitch
 };
 
+// Step kernel variants: TMA bulk-copy pipeline (needs nx % 8 == 0, nx >= 16),
+// or per-thread global loads (any size).
+constexpr int kPipeTma = 0;
+constexpr int kPipeLdg = 1;
+inline bool tma_pipeline_ok(int nx) { return nx % 8 == 0 && nx >= 16; }
+
+// Status bit a kernel sets when an mbarrier wait gave up (tf_lbm_check).
+constexpr int kStatusTimeout = 4;
+
 // Per-run constants of the step, in the compute type T.
 template <typename T>
 struct Consts {
@@ -30,12 +39,14 @@ struct Consts {
     // R_l = f_eq_l(href, 0) = r_axis (odd l) or r_diag (even l); minv = 1/mscale
     T mscale, minv, r_axis, r_diag;
     int n_exp, m_exp;
+    int* status;  // device word for kStatusTimeout (may be null)
 };
 
 // Launch shape of the fused step.
 struct Shape {
-    int block_x;  // 32, 64, 128, 256
-    int rows;     // rows per CTA
+    int block_x;   // 64, 128, 256
+    int rows;      // rows per CTA (band height)
+    int pipeline;  // kPipeTma or kPipeLdg
 };
 
 // Storage of the 8 moving populations.
@@ -49,7 +60,7 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
                         const Consts<float>* C32, const Consts<double>* C64, const Shape& S,
                         cudaStream_t st);
 // Resident CTAs per SM of the step kernel for a launch shape (0 if unknown).
-int step_blocks_per_sm(int store, int block_x, bool omega1, bool kfield);
+int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield);
 
 // Storage convention: plane 0 holds f_0 - href, planes 1..8 hold f_l (or its
 // 16-bit encoding, see Consts).  In

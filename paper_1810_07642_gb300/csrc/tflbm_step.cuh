@@ -158,46 +158,162 @@ __device__ __forceinline__ T film_pressure(const T* hn, const T* hc, const T* hs
     return -C.gamma * lap;
 }
 
+// ---------------------------------------------------------------------------
+// Force, collision and store of one node (both kernels).  pn, pc, ps are the
+// shared p rows at o+1, o, o-1 and t the node's slot in them; dh = h - href,
+// ih = 1/h, (jx, jy) the momentum, er the pull-sum residual, f the pulled
+// populations (used when omega != 1).  The node's storage offset is
+// row + x.
+template <typename SM, typename T, bool OMEGA1>
+__device__ __forceinline__ void collide_store(const T* pn, const T* pc, const T* ps, int t, T dh,
+                                              T ih, T jx, T jy, T er, const T (&f)[9],
+                                              T* __restrict__ fout0, SM* __restrict__ foutm,
+                                              int row, int x, int plane, const Consts<T>& C)
+{
+    constexpr bool NARROW = !std::is_same<SM, T>::value;
+    const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0), sixth = T(1.0 / 6.0);
+    // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
+    const T gpx = (pc[t + 1] - pc[t - 1]) * third
+                + ((pn[t + 1] - pn[t - 1]) + (ps[t + 1] - ps[t - 1])) * twelfth;
+    const T gpy = (pn[t] - ps[t]) * third
+                + ((pn[t + 1] - ps[t + 1]) + (pn[t - 1] - ps[t - 1])) * twelfth;
+    const T h = dh + C.href;
+    // Eqs. (force), (forcefric), (alphafric):
+    // nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
+    const T fr = fdiv(C.nu6, h * (T(2) * h + T(6) * C.delta) + T(3) * C.delta * C.delta);
+    const T Fx = h * (C.gx - gpx) - fr * jx;
+    const T Fy = h * (C.gy - gpy) - fr * jy;
+    // Eq. (equilibria) with e^2 = 1, written as S +- D per pair of opposite
+    // directions; source 3 w_l c_l . F.
+    const T ux = jx * ih, uy = jy * ih;
+    const T A = h * (C.g * h - (ux * ux + uy * uy)) * sixth;
+    const T Sx = A + T(0.5) * jx * ux;
+    const T Sy = A + T(0.5) * jy * uy;
+    const T a = ux + uy, b = uy - ux;
+    const T Sa = (A + T(0.5) * h * a * a) * T(0.25);
+    const T Sb = (A + T(0.5) * h * b * b) * T(0.25);
+    T o1, o2, o3, o4, o5, o6, o7, o8;
+    if (OMEGA1) {
+        const T Dx = (jx + Fx) * third, Dy = (jy + Fy) * third;
+        const T Da = ((jx + jy) + (Fx + Fy)) * twelfth;
+        const T Db = ((jy - jx) + (Fy - Fx)) * twelfth;
+        o1 = Sx + Dx; o5 = Sx - Dx;
+        o3 = Sy + Dy; o7 = Sy - Dy;
+        o2 = Sa + Da; o6 = Sa - Da;
+        o4 = Sb + Db; o8 = Sb - Db;
+    } else {
+        const T w = C.omega, m = T(1) - C.omega;
+        const T Dx = jx * third, Dy = jy * third;
+        const T Da = (jx + jy) * twelfth, Db = (jy - jx) * twelfth;
+        const T Qx = Fx * third, Qy = Fy * third;
+        const T Qa = (Fx + Fy) * twelfth, Qb = (Fy - Fx) * twelfth;
+        o1 = m * f[1] + w * (Sx + Dx) + Qx;
+        o5 = m * f[5] + w * (Sx - Dx) - Qx;
+        o3 = m * f[3] + w * (Sy + Dy) + Qy;
+        o7 = m * f[7] + w * (Sy - Dy) - Qy;
+        o2 = m * f[2] + w * (Sa + Da) + Qa;
+        o6 = m * f[6] + w * (Sa - Da) - Qa;
+        o4 = m * f[4] + w * (Sb + Db) + Qb;
+        o8 = m * f[8] + w * (Sb - Db) - Qb;
+    }
+    // In 16-bit storage, round the moving populations to what the readers
+    // will reconstruct before the rest population is formed.
+    SM q1, q2, q3, q4, q5, q6, q7, q8;
+    if constexpr (NARROW) {
+        auto narrow = [&](T& o, SM& q, T R) {
+            q = from_f<SM>((o - R) * C.mscale);
+            o = fmaf(to_f(q), C.minv, R);
+        };
+        narrow(o1, q1, C.r_axis); narrow(o3, q3, C.r_axis);
+        narrow(o5, q5, C.r_axis); narrow(o7, q7, C.r_axis);
+        narrow(o2, q2, C.r_diag); narrow(o4, q4, C.r_diag);
+        narrow(o6, q6, C.r_diag); narrow(o8, q8, C.r_diag);
+    }
+    // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l.  The
+    // error-free sums give the exact rounding residuals of the pull sum and
+    // of this subtraction.  With full-width storage they go to the opposite
+    // pair (1, 5), half each, so the stored populations sum to the pulled
+    // ones (mass conserved to roundings of small values) and the momentum is
+    // untouched; with 16-bit storage they are added to the rest population.
+    const T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
+    T o0v, e2;
+    two_sum(dh, -osum, o0v, e2);
+    if constexpr (NARROW) {
+        o0v += er + e2;
+    } else {
+        const T half_r = (er + e2) * T(0.5);
+        o1 += half_r;
+        o5 += half_r;
+        q1 = o1; q2 = o2; q3 = o3; q4 = o4; q5 = o5; q6 = o6; q7 = o7; q8 = o8;
+    }
+    const int i = row + x;
+    fout0[i] = o0v;
+    SM* om = foutm + i;
+    om[0] = q1;
+    om[plane] = q2;
+    om[2 * plane] = q3;
+    om[3 * plane] = q4;
+    om[4 * plane] = q5;
+    om[5 * plane] = q6;
+    om[6 * plane] = q7;
+    om[7 * plane] = q8;
+}
+
+// ---------------------------------------------------------------------------
+// Common geometry of one CTA: BX columns x0-2 .. x0+BX-3, one per thread
+// (neighbouring CTAs overlap by 4 columns, so each stores BX-4 columns and
+// needs no divergent halo work), marching down a band of rows.
+struct Band {
+    int x0, weff, ybeg, yend, R, dir, rstart;
+    bool hcol, pcol, ocol;
+};
+
+template <int BX>
+__device__ __forceinline__ Band make_band(const Geom& G, int t)
+{
+    Band b;
+    constexpr int W = BX - 4;
+    b.x0 = blockIdx.x * W;                      // first output column
+    b.weff = min(W, G.nx - b.x0);               // output columns of this CTA
+    b.hcol = t < b.weff + 4;                    // forms h
+    b.pcol = t >= 1 && t < b.weff + 3;          // forms p
+    b.ocol = t >= 2 && t < b.weff + 2;          // collides and stores
+    b.ybeg = (int)(((long long)blockIdx.y * G.ny) / gridDim.y);
+    b.yend = (int)(((long long)(blockIdx.y + 1) * G.ny) / gridDim.y);
+    // March direction: even bands go +y, odd bands -y, so two neighbouring
+    // bands read the rows around their common edge at the same time (both at
+    // the start or both at the end of the kernel) and the second read hits
+    // L2.  March step k forms h of row r(k) = rstart + k dir, the pressure of
+    // row r(k-1) and collides row r(k-3), for k = 0 .. R+4.
+    b.dir = (blockIdx.y & 1) ? -1 : 1;
+    b.R = b.yend - b.ybeg;
+    b.rstart = b.dir > 0 ? b.ybeg - 2 : b.yend + 1;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1: every thread loads its own nine pulled populations from global
+// memory, one row ahead of use (register prefetch).
 template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX, OMEGA1 ? 1024 / BX : 1)
+__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
 k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
        SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
-    constexpr bool NARROW = !std::is_same<SM, T>::value;  // 16-bit moving populations
-    constexpr int W = BX - 4;     // output columns per CTA
-    __shared__ T hsm[4][BX];      // h - href ring: slot t = column x0 - 2 + t
-    __shared__ T psm[4][BX];      // p ring, same columns
-
+    __shared__ T hsm[4][BX];  // h - href ring: slot t = column x0 - 2 + t
+    __shared__ T psm[4][BX];  // p ring, same columns
     const int t = threadIdx.x;
-    const int nx = G.nx, ny = G.ny, pitch = G.pitch;
-    const int plane = (int)G.plane;
-    const int x0 = blockIdx.x * W;                 // first output column
-    const int weff = min(W, nx - x0);              // output columns of this CTA
-    const bool hcol = t < weff + 4;                // forms h
-    const bool pcol = t >= 1 && t < weff + 3;      // forms p
-    const bool ocol = t >= 2 && t < weff + 2;      // collides and stores
-    const int ybeg = (int)(((long long)blockIdx.y * ny) / gridDim.y);
-    const int yend = (int)(((long long)(blockIdx.y + 1) * ny) / gridDim.y);
+    const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
+    const Band B = make_band<BX>(G, t);
     const bool disj = KFIELD || C.kappa_u != T(0);
+    const int dir = B.dir, R = B.R;
 
-    const int x = wrap_index(x0 - 2 + t, nx);
+    const int x = wrap_index(B.x0 - 2 + t, nx);
     const int xm = wrap_index(x - 1, nx), xp = wrap_index(x + 1, nx);
 
-    // March direction: even bands go +y, odd bands -y, so two neighbouring
-    // bands read the rows around their common edge at the same time (both at
-    // the start or both at the end of the kernel) and the second read hits L2.
-    // March step k forms h of row r(k) = r0 + k dir, the pressure of row
-    // r(k-1) and collides row r(k-3), for k = 0 .. R+4 (R = band rows).
-    const int dir = (blockIdx.y & 1) ? -1 : 1;
-    const int R = yend - ybeg;
-    const int rstart = dir > 0 ? ybeg - 2 : yend + 1;
-
     // wrapped indices of rows r(k-1), r(k), r(k+1), r(k+2)
-    int wm1 = wrap_index(rstart - dir, ny), w0 = wrap_index(rstart, ny);
-    int w1 = wrap_index(rstart + dir, ny), w2 = wrap_index(rstart + 2 * dir, ny);
+    int wm1 = wrap_index(B.rstart - dir, ny), w0 = wrap_index(B.rstart, ny);
+    int w1 = wrap_index(B.rstart + dir, ny), w2 = wrap_index(B.rstart + 2 * dir, ny);
 
-    // pulled populations of the next row, kappa of the next pressure row,
-    // and per-row values kept until the row is collided three rows later
     T v[9];
     T kap_n = C.kappa_u;
     T fv[4][9];
@@ -205,19 +321,14 @@ k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ 
 #pragma unroll
     for (int s = 0; s < 4; ++s) { jxv[s] = jyv[s] = ihv[s] = erv[s] = T(0); }
 
-    const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0), sixth = T(1.0 / 6.0);
-    const T one_m_omega = T(1) - C.omega;
-    const T d6 = T(6) * C.delta, d3sq = T(3) * C.delta * C.delta;
-
     // pull row w whose neighbours in march order are wb (behind) and wa (ahead)
     auto pull_row = [&](int wb, int w, int wa) {
         const int r0 = w * pitch;
         const int below = (dir > 0 ? wb : wa) - w, above = (dir > 0 ? wa : wb) - w;
         pull9<SM, T>(fin0, finm, plane, r0 + x, r0 + xm, r0 + xp, below * pitch, above * pitch, C, v);
     };
-    // prologue: loads of the first h row r(0) and kappa of row r(-1)
-    if (hcol) pull_row(wm1, w0, w1);
-    if (KFIELD && pcol) kap_n = kappa[(long long)wm1 * nx + x];
+    if (B.hcol) pull_row(wm1, w0, w1);
+    if (KFIELD && B.pcol) kap_n = kappa[(long long)wm1 * nx + x];
 
     auto body = [&](auto stage_c, int k) {
         constexpr int s = decltype(stage_c)::value;  // slot of row r(k) (and r(k-4))
@@ -226,7 +337,7 @@ k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ 
         constexpr int s3 = (s + 1) & 3;              // slot of row r(k-3)
         // ---- (A) h of row r(k); the loads of row r(k+1) go out before anything waits
         const T kap = kap_n;  // kappa of row r(k-1), loaded last step
-        if (hcol && k <= R + 3) {
+        if (B.hcol && k <= R + 3) {
             hsm[s][t] = sum9(v, erv[s]);
             jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
             jyv[s] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
@@ -235,113 +346,22 @@ k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ 
                 for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
             }
             if (k + 1 <= R + 3) pull_row(w0, w1, w2);
-            if (KFIELD && pcol) kap_n = kappa[(long long)w0 * nx + x];
+            if (KFIELD && B.pcol) kap_n = kappa[(long long)w0 * nx + x];
         }
         __syncthreads();
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
-        if (pcol && k >= 2 && k <= R + 3) {
+        if (B.pcol && k >= 2 && k <= R + 3) {
             const T ih = fdiv(T(1), hsm[s1][t] + C.href);
             ihv[s1] = ih;
             psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj);
         }
         // ---- (B2) force, collision and store of row r(k-3) (needs p rows r(k-4) .. r(k-2))
-        if (ocol && k >= 5) {
-            const int o = rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
-            const T* pn = dir > 0 ? psm[s2] : psm[s];  // row o + 1
-            const T* pcr = psm[s3];
-            const T* ps = dir > 0 ? psm[s] : psm[s2];  // row o - 1
-            // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
-            const T gpx = (pcr[t + 1] - pcr[t - 1]) * third
-                        + ((pn[t + 1] - pn[t - 1]) + (ps[t + 1] - ps[t - 1])) * twelfth;
-            const T gpy = (pn[t] - ps[t]) * third
-                        + ((pn[t + 1] - ps[t + 1]) + (pn[t - 1] - ps[t - 1])) * twelfth;
-            const T dh = hsm[s3][t];
-            const T h = dh + C.href;
-            const T ih = ihv[s3];
-            const T jx = jxv[s3], jy = jyv[s3];
-            // Eqs. (force), (forcefric), (alphafric):
-            // nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
-            const T fr = fdiv(C.nu6, h * (T(2) * h + d6) + d3sq);
-            const T Fx = h * (C.gx - gpx) - fr * jx;
-            const T Fy = h * (C.gy - gpy) - fr * jy;
-            // Eq. (equilibria) with e^2 = 1, written as S +- D per pair of
-            // opposite directions; source 3 w_l c_l . F.
-            const T ux = jx * ih, uy = jy * ih;
-            const T A = h * (C.g * h - (ux * ux + uy * uy)) * sixth;
-            const T Sx = A + T(0.5) * jx * ux;
-            const T Sy = A + T(0.5) * jy * uy;
-            const T a = ux + uy, b = uy - ux;
-            const T Sa = (A + T(0.5) * h * a * a) * T(0.25);
-            const T Sb = (A + T(0.5) * h * b * b) * T(0.25);
-            T o1, o2, o3, o4, o5, o6, o7, o8;
-            if (OMEGA1) {
-                const T Dx = (jx + Fx) * third, Dy = (jy + Fy) * third;
-                const T Da = ((jx + jy) + (Fx + Fy)) * twelfth;
-                const T Db = ((jy - jx) + (Fy - Fx)) * twelfth;
-                o1 = Sx + Dx; o5 = Sx - Dx;
-                o3 = Sy + Dy; o7 = Sy - Dy;
-                o2 = Sa + Da; o6 = Sa - Da;
-                o4 = Sb + Db; o8 = Sb - Db;
-            } else {
-                const T w = C.omega;
-                const T Dx = jx * third, Dy = jy * third;
-                const T Da = (jx + jy) * twelfth, Db = (jy - jx) * twelfth;
-                const T Qx = Fx * third, Qy = Fy * third;
-                const T Qa = (Fx + Fy) * twelfth, Qb = (Fy - Fx) * twelfth;
-                const T(&f)[9] = fv[s3];
-                o1 = one_m_omega * f[1] + w * (Sx + Dx) + Qx;
-                o5 = one_m_omega * f[5] + w * (Sx - Dx) - Qx;
-                o3 = one_m_omega * f[3] + w * (Sy + Dy) + Qy;
-                o7 = one_m_omega * f[7] + w * (Sy - Dy) - Qy;
-                o2 = one_m_omega * f[2] + w * (Sa + Da) + Qa;
-                o6 = one_m_omega * f[6] + w * (Sa - Da) - Qa;
-                o4 = one_m_omega * f[4] + w * (Sb + Db) + Qb;
-                o8 = one_m_omega * f[8] + w * (Sb - Db) - Qb;
-            }
-            // In 16-bit storage, round the moving populations to what the
-            // readers will reconstruct before the rest population is formed.
-            SM q1, q2, q3, q4, q5, q6, q7, q8;
-            if constexpr (NARROW) {
-                auto narrow = [&](T& o, SM& q, T R) {
-                    q = from_f<SM>((o - R) * C.mscale);
-                    o = fmaf(to_f(q), C.minv, R);
-                };
-                narrow(o1, q1, C.r_axis); narrow(o3, q3, C.r_axis);
-                narrow(o5, q5, C.r_axis); narrow(o7, q7, C.r_axis);
-                narrow(o2, q2, C.r_diag); narrow(o4, q4, C.r_diag);
-                narrow(o6, q6, C.r_diag); narrow(o8, q8, C.r_diag);
-            }
-            // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l.
-            // The error-free sums give the exact rounding residuals of the
-            // pull sum and of this subtraction.  With full-width storage they
-            // go to the opposite pair (1, 5), half each, so the stored
-            // populations sum to the pulled ones (mass conserved to roundings
-            // of small values) and the momentum is untouched; with 16-bit
-            // storage they are added to the rest population itself.
-            const T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
-            T o0v, e2;
-            two_sum(dh, -osum, o0v, e2);
-            if constexpr (NARROW) {
-                o0v += erv[s3] + e2;
-            } else {
-                const T half_r = (erv[s3] + e2) * T(0.5);
-                o1 += half_r;
-                o5 += half_r;
-                q1 = o1; q2 = o2; q3 = o3; q4 = o4; q5 = o5; q6 = o6; q7 = o7; q8 = o8;
-            }
-            const int io = o * pitch + x;
-            fout0[io] = o0v;
-            SM* om = foutm + io;
-            om[0] = q1;
-            om[plane] = q2;
-            om[2 * plane] = q3;
-            om[3 * plane] = q4;
-            om[4 * plane] = q5;
-            om[5 * plane] = q6;
-            om[6 * plane] = q7;
-            om[7 * plane] = q8;
+        if (B.ocol && k >= 5) {
+            const int o = B.rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
+            collide_store<SM, T, OMEGA1>(dir > 0 ? psm[s2] : psm[s], psm[s3], dir > 0 ? psm[s] : psm[s2], t,
+                                         hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fv[s3],
+                                         fout0, foutm, o * pitch, x, plane, C);
         }
-        // advance the wrapped row window
         wm1 = w0;
         w0 = w1;
         w1 = w2;
@@ -362,35 +382,313 @@ k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Kernel 2: the nine row segments each march step needs are streamed into
+// shared memory by the tensor memory accelerator (cp.async.bulk, one issuing
+// thread, completion on an mbarrier), four steps ahead of use; threads read
+// their shifted populations from shared memory.  Memory-level parallelism no
+// longer depends on registers or on the number of resident warps.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(b))
+        : "memory");
+}
+
+constexpr int kStages = 4;           // TMA pipeline depth, in march steps
+constexpr int kWaitLimit = 1 << 22;  // polls of one mbarrier before giving up
+
+// Shared-memory layout of one pipeline stage: plane 0 (compute type) then the
+// 8 moving planes (storage type), LMAX elements each.  LMAX covers the
+// segment [x0-3, x0+W+3) rounded out to 16-byte boundaries.
 template <typename SM, typename T, int BX>
-cudaError_t launch_step_bx(const T* fin0, const SM* finm, T* fout0, SM* foutm, const T* kappa,
-                           const Geom& G, const Consts<T>& C, int rows, cudaStream_t st)
+struct TmaLayout {
+    static constexpr int A = 16 / (sizeof(SM) < sizeof(T) ? sizeof(SM) : sizeof(T));
+    static constexpr int LMAX = BX + 16;
+    static constexpr int B0 = LMAX * (int)sizeof(T);
+    static constexpr int BM = LMAX * (int)sizeof(SM);
+    static constexpr int STAGE = (B0 + 8 * BM + 127) / 128 * 128;
+    static constexpr int BYTES = kStages * STAGE;
+    static_assert(B0 % 16 == 0 && BM % 16 == 0, "stage planes must stay 16-byte aligned");
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Bulk copies of one march step, issued by warp 0: lane 0 arms the stage's
+// mbarrier with the byte count, then lane l (0..8) copies plane l from row
+// y - c_ly, lattice columns [a0, a1), into its slot of the stage.  Columns
+// outside [0, nx) come from the periodic images, so a segment is copied in up
+// to three pieces (the host only selects this kernel when nx is a multiple of
+// 8 elements, which keeps every piece 16-byte aligned).
+template <typename SM, typename T>
+__device__ __noinline__ void issue_step(unsigned char* stage, uint64_t* bar, const T* fin0,
+                                        const SM* finm, int plane, int pitch, int nx, int ny, int row,
+                                        int a0, int a1, int b0, int bm, uint32_t bytes)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_arrive_tx(bar, bytes);
+    __syncwarp();
+    if (lane < 9) {
+        // c_ly of population l: 0 0 1 1 1 0 -1 -1 -1
+        const int cy = (lane >= 2 && lane <= 4) ? 1 : (lane >= 6 ? -1 : 0);
+        int r = row - cy;
+        r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const char* src;
+        int es;
+        unsigned char* dst;
+        if (lane == 0) {
+            src = reinterpret_cast<const char*>(fin0 + (long long)r * pitch);
+            es = (int)sizeof(T);
+            dst = stage;
+        } else {
+            src = reinterpret_cast<const char*>(finm + ((long long)(lane - 1) * plane + (long long)r * pitch));
+            es = (int)sizeof(SM);
+            dst = stage + b0 + (lane - 1) * bm;
+        }
+        int c = a0;
+        if (c < 0) {  // left periodic image
+            bulk_g2s(dst, src + (long long)(c + nx) * es, (uint32_t)(-c * es), bar);
+            dst += -c * es;
+            c = 0;
+        }
+        const int e = a1 < nx ? a1 : nx;
+        bulk_g2s(dst, src + (long long)c * es, (uint32_t)((e - c) * es), bar);
+        dst += (e - c) * es;
+        if (a1 > nx) bulk_g2s(dst, src, (uint32_t)((a1 - nx) * es), bar);  // right image
+    }
+}
+
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
+k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
+           SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
+{
+    using L = TmaLayout<SM, T, BX>;
+    extern __shared__ __align__(128) unsigned char stage_mem[];
+    __shared__ T hsm[4][BX];  // h - href ring: slot t = column x0 - 2 + t
+    __shared__ T psm[4][BX];  // p ring, same columns
+    __shared__ __align__(8) uint64_t bars[kStages];
+
+    const int t = threadIdx.x;
+    const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
+    const Band B = make_band<BX>(G, t);
+    const bool disj = KFIELD || C.kappa_u != T(0);
+    const int dir = B.dir, R = B.R;
+    const int x = wrap_index(B.x0 - 2 + t, nx);
+
+    // the row segment [a0, a1) copied per plane; column X sits at X - a0
+    const int a0 = floor_div(B.x0 - 3, L::A) * L::A;
+    const int a1 = (B.x0 + B.weff + 3 + L::A - 1) / L::A * L::A;
+    const int col = t + B.x0 - 2 - a0;
+    const uint32_t bytes_step = (uint32_t)(a1 - a0) * (uint32_t)(sizeof(T) + 8 * sizeof(SM));
+    auto issue = [&](int j) {  // march step j (h row r(j)) into stage j % kStages
+        const int st = j & (kStages - 1);
+        issue_step<SM, T>(stage_mem + st * L::STAGE, &bars[st], fin0, finm, plane, pitch, nx, ny,
+                          wrap_index(B.rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step);
+    };
+    bool timed_out = false;
+
+    if (t == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (t < 32)
+        for (int j = 0; j < kStages && j <= R + 3; ++j) issue(j);
+
+    int wk = wrap_index(B.rstart, ny);  // wrapped index of row r(k)
+    T kap_n = C.kappa_u;
+    if (KFIELD && B.pcol) kap_n = kappa[(long long)wrap_index(B.rstart - dir, ny) * nx + x];
+    T fv[4][9];
+    T jxv[4], jyv[4], ihv[4], erv[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) { jxv[s] = jyv[s] = ihv[s] = erv[s] = T(0); }
+
+    auto body = [&](auto stage_c, int k) {
+        constexpr int s = decltype(stage_c)::value;  // ring slot and pipeline stage of row r(k)
+        constexpr int s1 = (s + 3) & 3;              // slot of row r(k-1)
+        constexpr int s2 = (s + 2) & 3;              // slot of row r(k-2)
+        constexpr int s3 = (s + 1) & 3;              // slot of row r(k-3)
+        const T kap = kap_n;                         // kappa of row r(k-1)
+        // ---- (A) h of row r(k) from the stage that holds its pulled rows
+        if (k <= R + 3) {
+            const uint32_t parity = (uint32_t)(k / kStages) & 1u;
+            int it = 0;
+            while (!mbar_test(&bars[s], parity)) {
+                if (++it >= kWaitLimit) {
+                    timed_out = true;
+                    break;
+                }
+            }
+            if (B.hcol) {
+                const unsigned char* base = stage_mem + s * L::STAGE;
+                const T* p0 = reinterpret_cast<const T*>(base);
+                const SM* pm = reinterpret_cast<const SM*>(base + L::B0);
+                constexpr int M = L::LMAX;
+                // population l at column X comes from X - c_lx
+                T v[9];
+                v[0] = p0[col];
+                v[1] = load_moving(pm[0 * M + col - 1], 1, C);
+                v[2] = load_moving(pm[1 * M + col - 1], 2, C);
+                v[3] = load_moving(pm[2 * M + col], 3, C);
+                v[4] = load_moving(pm[3 * M + col + 1], 4, C);
+                v[5] = load_moving(pm[4 * M + col + 1], 5, C);
+                v[6] = load_moving(pm[5 * M + col + 1], 6, C);
+                v[7] = load_moving(pm[6 * M + col], 7, C);
+                v[8] = load_moving(pm[7 * M + col - 1], 8, C);
+                hsm[s][t] = sum9(v, erv[s]);
+                jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
+                jyv[s] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
+                if (!OMEGA1) {
+#pragma unroll
+                    for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
+                }
+                if (KFIELD && B.pcol) kap_n = kappa[(long long)wk * nx + x];  // row r(k), used next step
+            }
+        }
+        __syncthreads();
+        // every thread is done with this stage: refill it for step k + kStages
+        if (t < 32 && k + kStages <= R + 3) issue(k + kStages);
+        // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
+        if (B.pcol && k >= 2 && k <= R + 3) {
+            const T ih = fdiv(T(1), hsm[s1][t] + C.href);
+            ihv[s1] = ih;
+            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj);
+        }
+        // ---- (B2) force, collision and store of row r(k-3)
+        if (B.ocol && k >= 5) {
+            const int o = B.rstart + (k - 3) * dir;
+            collide_store<SM, T, OMEGA1>(dir > 0 ? psm[s2] : psm[s], psm[s3], dir > 0 ? psm[s] : psm[s2], t,
+                                         hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fv[s3],
+                                         fout0, foutm, o * pitch, x, plane, C);
+        }
+        wk += dir;
+        wk = wk == ny ? 0 : (wk < 0 ? ny - 1 : wk);
+    };
+
+    const int last = R + 4;
+    for (int k = 0;;) {
+        body(std::integral_constant<int, 0>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 1>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 2>{}, k);
+        if (++k > last) break;
+        body(std::integral_constant<int, 3>{}, k);
+        if (++k > last) break;
+    }
+
+    if (timed_out) {
+        // report, then give the copies still in flight a bounded chance to
+        // land before the CTA's shared memory is released
+        if (C.status) atomicOr(C.status, kStatusTimeout);
+        if (t == 0) {
+            for (int s = 0; s < kStages; ++s) {
+                const int jl = (R + 3) - ((((R + 3) - s) % kStages + kStages) % kStages);
+                if (jl >= 0) {
+                    int it = 0;
+                    while (!mbar_test(&bars[s], (uint32_t)(jl / kStages) & 1u) && ++it < kWaitLimit) {
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+template <typename SM, typename T, int BX, bool OM1, bool KF>
+cudaError_t launch_one(int pipeline, dim3 grid, const T* fin0, const SM* finm, T* fout0, SM* foutm,
+                       const T* kappa, const Geom& G, const Consts<T>& C, cudaStream_t st)
+{
+    if (pipeline == kPipeTma) {
+        using L = TmaLayout<SM, T, BX>;
+        static bool attr = false;  // one attribute call per instantiation
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_step_tma<SM, T, BX, OM1, KF>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_step_tma<SM, T, BX, OM1, KF><<<grid, BX, L::BYTES, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+    } else {
+        k_step<SM, T, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+    }
+    return cudaGetLastError();
+}
+
+template <typename SM, typename T, int BX>
+cudaError_t launch_step_bx(int pipeline, const T* fin0, const SM* finm, T* fout0, SM* foutm,
+                           const T* kappa, const Geom& G, const Consts<T>& C, int rows, cudaStream_t st)
 {
     int bands = (G.ny + rows - 1) / rows;
     if (bands > 65535) bands = 65535;
     dim3 grid((G.nx + BX - 5) / (BX - 4), bands);
     const bool om1 = (C.omega == T(1));
     if (kappa) {
-        if (om1) k_step<SM, T, BX, true, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-        else k_step<SM, T, BX, false, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-    } else {
-        if (om1) k_step<SM, T, BX, true, false><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-        else k_step<SM, T, BX, false, false><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+        if (om1) return launch_one<SM, T, BX, true, true>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+        return launch_one<SM, T, BX, false, true>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
     }
-    return cudaGetLastError();
+    if (om1) return launch_one<SM, T, BX, true, false>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+    return launch_one<SM, T, BX, false, false>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
 }
 
 // Resident CTAs per SM of one instantiation (for sizing the grid).
-template <typename SM, typename T, int BX>
-int blocks_per_sm_bx(bool omega1, bool kfield)
+template <typename SM, typename T, int BX, bool OM1, bool KF>
+int bps_one(int pipeline)
 {
     int n = 0;
     cudaError_t e;
-    if (kfield) e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, true, true>, BX, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, false, true>, BX, 0);
-    else e = omega1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, true, false>, BX, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, false, false>, BX, 0);
+    if (pipeline == kPipeTma) {
+        using L = TmaLayout<SM, T, BX>;
+        cudaFuncSetAttribute(k_step_tma<SM, T, BX, OM1, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             L::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tma<SM, T, BX, OM1, KF>, BX, L::BYTES);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, OM1, KF>, BX, 0);
+    }
     return e == cudaSuccess ? n : 0;
+}
+
+template <typename SM, typename T, int BX>
+int blocks_per_sm_bx(int pipeline, bool omega1, bool kfield)
+{
+    if (kfield) return omega1 ? bps_one<SM, T, BX, true, true>(pipeline) : bps_one<SM, T, BX, false, true>(pipeline);
+    return omega1 ? bps_one<SM, T, BX, true, false>(pipeline) : bps_one<SM, T, BX, false, false>(pipeline);
 }
 
 }  // namespace tflbm

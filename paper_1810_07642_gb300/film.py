@@ -110,12 +110,13 @@ class ThinFilm:
     @property
     def launch(self):
         l = L.tf_lbm_get_launch(self.handle)
-        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, pipeline=l.pipeline)
 
-    def set_launch(self, block_x=None, rows=None, graph_chunk=None):
+    def set_launch(self, block_x=None, rows=None, graph_chunk=None, pipeline=None):
         cur = self.launch
         L.tf_lbm_set_launch(self.handle, block_x or cur["block_x"], rows or cur["rows"],
-                            cur["graph_chunk"] if graph_chunk is None else graph_chunk)
+                            cur["graph_chunk"] if graph_chunk is None else graph_chunk,
+                            cur["pipeline"] if pipeline is None else pipeline)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -128,16 +128,19 @@ def test_parity_patterned_dewetting_256_fp32():
 @pytest.mark.parametrize("shape", [dict(block_x=64, rows=1), dict(block_x=64, rows=5),
                                    dict(block_x=64, rows=7, graph_chunk=4),
                                    dict(block_x=128, rows=64), dict(block_x=256, rows=17),
-                                   dict(block_x=128, rows=3, graph_chunk=4)])
+                                   dict(block_x=128, rows=3, graph_chunk=4),
+                                   dict(block_x=64, rows=9, pipeline=0),
+                                   dict(block_x=128, rows=33, pipeline=0)])
 def test_launch_shape_does_not_change_results(shape):
     """Every node does the same arithmetic in the same order whatever the band
-    height or graph chunking, so with the same CTA width results are bitwise
-    identical.  Another CTA width is another instantiation of the kernel, in
-    which the compiler may fuse multiply-adds differently: there results
-    agree to rounding (1e-6 relative after 23 steps)."""
-    h0, th, p = inputs.small_random(300, 141, seed=9, amp=0.05)
+    height or graph chunking, so with the same CTA width and load pipeline
+    results are bitwise identical.  Another CTA width or pipeline is another
+    kernel instantiation, in which the compiler may fuse multiply-adds
+    differently: there results agree to rounding (1e-6 relative after 23
+    steps)."""
+    h0, th, p = inputs.small_random(304, 141, seed=9, amp=0.05)
     ref = ThinFilm(p, h0, th)
-    ref.set_launch(block_x=64, rows=64, graph_chunk=0)
+    ref.set_launch(block_x=64, rows=64, graph_chunk=0, pipeline=1)
     ref.step(23)
     other = ThinFilm(p, h0, th)
     other.set_launch(**shape)
@@ -145,10 +148,20 @@ def test_launch_shape_does_not_change_results(shape):
     a, b = ref.get_state(), other.get_state()
     torch.cuda.synchronize()
     d = (a - b).abs()
-    if shape["block_x"] == 64:
+    if shape["block_x"] == 64 and shape.get("pipeline", 1) == 1:
         assert torch.equal(a, b), (d.max().item(), (d > 0).sum().item())
     else:
         assert d.max().item() <= 1e-6 * a.abs().max().item()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f16"])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (130, 70), (3, 3)])
+def test_parity_per_thread_load_pipeline(dtype, nx, ny):
+    """The per-thread-load kernel (pipeline 1, the default) against the oracle."""
+    h0, th, p = inputs.small_random(nx, ny, seed=nx + ny, amp=0.05)
+    p.update(tau=0.9, g=2e-4, gx_body=2e-5, delta=1.0)
+    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=1))
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
 
 
 # ------------------------------------------------- 16-bit population storage
@@ -292,6 +305,29 @@ def test_state_roundtrip_resumes_bitwise():
     a.step(9)
     b.step(9)
     assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_bulk_copy_pipeline_needs_nx_multiple_of_8():
+    h0, th, p = inputs.small_random(300, 20, seed=1)
+    sim = ThinFilm(p, h0, th)
+    assert sim.launch["pipeline"] == 1
+    with pytest.raises(L.TfLbmError):
+        sim.set_launch(pipeline=0)
+    h0, th, p = inputs.small_random(304, 20, seed=1)
+    sim = ThinFilm(p, h0, th)
+    sim.set_launch(pipeline=0)
+    assert sim.launch["pipeline"] == 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f16", "bf16"])
+@pytest.mark.parametrize("nx,ny", [(64, 48), (200, 33), (16, 9)])
+def test_parity_bulk_copy_pipeline(dtype, nx, ny):
+    """The bulk-copy (TMA) kernel against the oracle, including lattices whose
+    strips wrap on both sides."""
+    h0, th, p = inputs.small_random(nx, ny, seed=nx * 7 + ny, amp=0.05)
+    p.update(tau=0.9 if dtype == "f64" else 1.0, g=2e-4, gx_body=2e-5, delta=1.0)
+    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=0))
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
 
 
 def test_invalid_arguments_are_rejected():
