@@ -82,6 +82,8 @@ def lib():
         L.orc_step.argtypes = [_P, _D, _D, ctypes.c_int64]
         L.orc_mass.argtypes = [_P, _D]
         L.orc_mass.restype = ctypes.c_double
+        L.orc_adjoint_step.argtypes = [_P, _D, _D, _D, _D, _D]
+        L.orc_adjoint_init.argtypes = [_P, _D, _D, _D]
         L.orc_num_threads.restype = ctypes.c_int32
         L.orc_set_num_threads.argtypes = [ctypes.c_int32]
         _lib = L
@@ -220,6 +222,54 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     lib().orc_set_num_threads(int(n))
+
+
+def adjoint_step(cfg: Config, kap: np.ndarray, f_t: np.ndarray, a_next: np.ndarray,
+                 grad_kappa: np.ndarray):
+    """dL/df(t) from dL/df(t+1) for the step taken from the post-streaming
+    state f_t; adds the step's contribution to grad_kappa (in place)."""
+    kap = np.ascontiguousarray(np.broadcast_to(np.asarray(kap, np.float64), (cfg.ny, cfg.nx)))
+    f_t = np.ascontiguousarray(f_t, np.float64)
+    a_next = np.ascontiguousarray(a_next, np.float64)
+    assert grad_kappa.flags.c_contiguous and grad_kappa.dtype == np.float64
+    a = np.empty_like(a_next)
+    p = cfg.cparams()
+    lib().orc_adjoint_step(ctypes.byref(p), _ptr(kap), _ptr(f_t), _ptr(a_next), _ptr(a),
+                           _ptr(grad_kappa))
+    return a
+
+
+def adjoint_init(cfg: Config, h0: np.ndarray, a0: np.ndarray) -> np.ndarray:
+    """dL/dh0 from dL/df(0), for f(0) = f_eq(h0, 0)."""
+    h0 = np.ascontiguousarray(h0, np.float64)
+    out = np.empty_like(h0)
+    p = cfg.cparams()
+    lib().orc_adjoint_init(ctypes.byref(p), _ptr(h0), _ptr(np.ascontiguousarray(a0)), _ptr(out))
+    return out
+
+
+def dkappa_dtheta(cfg: Config, theta) -> np.ndarray:
+    """d kappa / d theta of Eq. (disjoiningP): sin(theta) (n-1)(m-1)/((n-m) h_*)."""
+    c = (cfg.n_exp - 1) * (cfg.m_exp - 1) / ((cfg.n_exp - cfg.m_exp) * cfg.hstar)
+    return np.sin(np.asarray(theta, np.float64)) * c
+
+
+def gradient(cfg: Config, h0: np.ndarray, theta, nsteps: int, seed):
+    """Reverse-mode gradient of a loss of the final post-streaming state.
+
+    seed(f_T) -> (L, dL/df_T).  Keeps every intermediate state (small cases
+    only).  Returns (L, dL/dtheta, dL/dh0, dL/dkappa)."""
+    theta = np.ascontiguousarray(np.broadcast_to(np.asarray(theta, np.float64), (cfg.ny, cfg.nx)))
+    kap = kappa_field(cfg, theta)
+    states = [init(cfg, h0)]
+    for _ in range(nsteps):
+        states.append(step(cfg, kap, states[-1].copy(), 1))
+    L, a = seed(states[-1])
+    gk = np.zeros((cfg.ny, cfg.nx))
+    for t in range(nsteps - 1, -1, -1):
+        a = adjoint_step(cfg, kap, states[t], a, gk)
+    gh0 = adjoint_init(cfg, h0, a)
+    return L, gk * dkappa_dtheta(cfg, theta), gh0, gk
 
 
 def run(cfg: Config, h0: np.ndarray, theta, nsteps: int):

@@ -335,3 +335,134 @@ void orc_set_num_threads(int32_t n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------ adjoint */
+
+/* Reverse-mode derivative of one step.  The state is the post-streaming
+ * f(t); one step is f(t+1) = S(C(f(t))), C the collision of Eq. (LBE) with
+ * the force of Eq. (force), S the streaming.  Given a_next = dL/df(t+1), this
+ * writes a = dL/df(t) = (dS C / df)^T a_next and adds (dS C / dkappa)^T a_next
+ * to grad_kappa.  The derivative is taken of the same phases as orc_step:
+ *   mu_l(x)   = a_next_l(x + c_l)                    (transpose of streaming)
+ *   collision f*_l = (1-w) f_l + w E_l(h, j) + 3 w_l c_l . F, with
+ *     E_l written in (h, j): E_0 = h - 5gh^2/6 - 2|j|^2/(3h),
+ *     axis: gh^2/6 + c.j/3 + (c.j)^2/(2h) - |j|^2/(6h),
+ *     diagonal: gh^2/24 + c.j/12 + (c.j)^2/(8h) - |j|^2/(24h);
+ *   F = h (G - grad p) - fr(h) j,  fr = 6 nu / (2h^2 + 6 delta h + 3 delta^2);
+ *   p = -gamma (lap h + s kappa ((hstar/h)^n - (hstar/h)^m));
+ *   h = sum_l f_l,  j = sum_l c_l f_l.
+ * Each line of the derivation is a plain loop over the lattice below. */
+void orc_adjoint_step(const orc_params* P, const double* kappa, const double* f,
+                      const double* a_next, double* a, double* grad_kappa)
+{
+    lattice_setup();
+    const int32_t nx = P->nx, ny = P->ny;
+    const int64_t N = (int64_t)nx * ny;
+    const double omega = 1.0 / P->tau, nu = (P->tau - 0.5) / 3.0, g = P->g;
+    const double s = (double)P->pi_sign;
+    double* buf = malloc(sizeof(double) * 28 * N);
+    double *h = buf, *jx = buf + N, *jy = buf + 2 * N, *ux = buf + 3 * N, *uy = buf + 4 * N,
+           *lap = buf + 5 * N, *p = buf + 6 * N, *gpx = buf + 7 * N, *gpy = buf + 8 * N,
+           *mu = buf + 9 * N, /* 9 fields */
+           *aH = buf + 18 * N, *aJx = buf + 19 * N, *aJy = buf + 20 * N, *agx = buf + 21 * N,
+           *agy = buf + 22 * N, *ap = buf + 23 * N, *alap = buf + 24 * N, *Fx = buf + 25 * N,
+           *Fy = buf + 26 * N;
+
+    /* forward quantities at time t */
+    orc_moments(P, f, h, ux, uy);
+    /* j as the plain population sums, as the forward defines it */
+    for (int64_t i = 0; i < N; ++i) {
+        double sx = 0.0, sy = 0.0;
+        for (int l = 0; l < 9; ++l) { sx += CX[l] * f[l * N + i]; sy += CY[l] * f[l * N + i]; }
+        jx[i] = sx; jy[i] = sy;
+    }
+    pressure_force(P, kappa, h, ux, uy, lap, p, gpx, gpy, Fx, Fy);
+
+    /* transpose of streaming: mu_l(x) = a_next_l(x + c_l) */
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x)
+            for (int l = 0; l < 9; ++l)
+                mu[l * N + y * nx + x] = a_next[l * N + wrap(y + CY[l], ny) * nx + wrap(x + CX[l], nx)];
+
+    /* collision and force, node by node */
+    for (int64_t i = 0; i < N; ++i) {
+        const double hh = h[i], Jx = jx[i], Jy = jy[i], j2 = Jx * Jx + Jy * Jy;
+        double aFx = 0.0, aFy = 0.0, ah = 0.0, ajx = 0.0, ajy = 0.0;
+        for (int l = 0; l < 9; ++l) {
+            const double m = mu[l * N + i];
+            aFx += 3.0 * W[l] * CX[l] * m;
+            aFy += 3.0 * W[l] * CY[l] * m;
+            const double am = omega * m;  /* adjoint of E_l */
+            const double cj = CX[l] * Jx + CY[l] * Jy;
+            double dEdh, dEdjx, dEdjy;
+            if (l == 0) {
+                dEdh = 1.0 - 5.0 * g * hh / 3.0 + 2.0 * j2 / (3.0 * hh * hh);
+                dEdjx = -4.0 * Jx / (3.0 * hh);
+                dEdjy = -4.0 * Jy / (3.0 * hh);
+            } else if (l % 2 == 1) {
+                dEdh = g * hh / 3.0 - cj * cj / (2.0 * hh * hh) + j2 / (6.0 * hh * hh);
+                dEdjx = CX[l] / 3.0 + cj * CX[l] / hh - Jx / (3.0 * hh);
+                dEdjy = CY[l] / 3.0 + cj * CY[l] / hh - Jy / (3.0 * hh);
+            } else {
+                dEdh = g * hh / 12.0 - cj * cj / (8.0 * hh * hh) + j2 / (24.0 * hh * hh);
+                dEdjx = CX[l] / 12.0 + cj * CX[l] / (4.0 * hh) - Jx / (12.0 * hh);
+                dEdjy = CY[l] / 12.0 + cj * CY[l] / (4.0 * hh) - Jy / (12.0 * hh);
+            }
+            ah += am * dEdh;
+            ajx += am * dEdjx;
+            ajy += am * dEdjy;
+        }
+        /* F = h (G - grad p) - fr(h) j */
+        const double den = 2.0 * hh * hh + 6.0 * P->delta * hh + 3.0 * P->delta * P->delta;
+        const double fr = 6.0 * nu / den;
+        const double dfr = -6.0 * nu * (4.0 * hh + 6.0 * P->delta) / (den * den);
+        ah += aFx * (P->gx_body - gpx[i]) + aFy * (P->gy_body - gpy[i]) - dfr * (aFx * Jx + aFy * Jy);
+        ajx += -fr * aFx;
+        ajy += -fr * aFy;
+        agx[i] = -hh * aFx;
+        agy[i] = -hh * aFy;
+        aH[i] = ah;
+        aJx[i] = ajx;
+        aJy[i] = ajy;
+    }
+    /* transpose of Eq. (derivative): ap(y) = sum_l 3 w_l c_l . ag(y - c_l) */
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            double sum = 0.0;
+            for (int l = 0; l < 9; ++l) {
+                const int64_t k = wrap(y - CY[l], ny) * nx + wrap(x - CX[l], nx);
+                sum += 3.0 * W[l] * (CX[l] * agx[k] + CY[l] * agy[k]);
+            }
+            ap[y * nx + x] = sum;
+        }
+    /* p = -gamma (lap + s Pi): Pi contributes to h and to kappa */
+    for (int64_t i = 0; i < N; ++i) {
+        alap[i] = -P->gamma * ap[i];
+        const double api = -P->gamma * s * ap[i];
+        const double r = P->hstar / h[i];
+        const double rn = pow(r, (double)P->n_exp), rm = pow(r, (double)P->m_exp);
+        grad_kappa[i] += api * (rn - rm);
+        aH[i] += api * kappa[i] * (-(double)P->n_exp * rn + (double)P->m_exp * rm) / h[i];
+    }
+    /* Eq. (n_laplace) is symmetric: its transpose is itself */
+    orc_laplacian(nx, ny, alap, p); /* p reused as scratch */
+    for (int64_t i = 0; i < N; ++i) aH[i] += p[i];
+    /* h = sum_l f_l, j = sum_l c_l f_l, and the (1 - w) f_l term */
+    for (int64_t i = 0; i < N; ++i)
+        for (int l = 0; l < 9; ++l)
+            a[l * N + i] = aH[i] + CX[l] * aJx[i] + CY[l] * aJy[i] + (1.0 - omega) * mu[l * N + i];
+    free(buf);
+}
+
+/* dL/dh0 from dL/df(0) for f_l(x, 0) = f_eq_l(h0(x), 0). */
+void orc_adjoint_init(const orc_params* P, const double* h0, const double* a0, double* grad_h0)
+{
+    lattice_setup();
+    const int64_t N = (int64_t)P->nx * P->ny;
+    for (int64_t i = 0; i < N; ++i) {
+        const double hh = h0[i];
+        double s = a0[i] * (1.0 - 5.0 * P->g * hh / 3.0);
+        for (int l = 1; l < 9; ++l) s += a0[l * N + i] * P->g * hh * ((l % 2 == 1) ? 1.0 / 3.0 : 1.0 / 12.0);
+        grad_h0[i] = s;
+    }
+}
