@@ -171,6 +171,82 @@ def oracle_cpu_baseline(budget_s: float = 15.0):
                       f"({dt:.1f} s, {O.num_threads()} OpenMP threads)"}
 
 
+def storage_variants(steps: int = 2000):
+    """MLUPS of the 16-bit storage forms on the bench workload (same launch
+    rules), and the relative Linf error on h of every storage form against
+    the FP64 oracle on the same workload reduced to 256^2, 1000 steps."""
+    import torch
+    import oracle as O
+    from paper_1810_07642_gb300 import inputs
+    from paper_1810_07642_gb300.film import ThinFilm
+    out = {}
+    h0, th, p = inputs.patterned_dewetting(N_SIDE, seed=0)
+    for dt, bpl in (("f32", 76), ("f16", 44), ("bf16", 44)):
+        sim = ThinFilm(p, h0, th, dtype=dt)
+        sim.step(50)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        sim.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[dt] = {"mlups": N_SIDE * N_SIDE / ms / 1e3, "bytes_per_lu": bpl,
+                   "gbs": bpl * N_SIDE * N_SIDE / ms / 1e6}
+        sim.close()
+    hs, ths, ps = inputs.patterned_dewetting(256, seed=1)
+    cfg = O.Config(**{k: v for k, v in ps.items() if k in O.Config.__dataclass_fields__})
+    _, ho, _, _ = O.run(cfg, hs, ths, 1000)
+    for dt in ("f32", "f16", "bf16"):
+        sim = ThinFilm(ps, hs, ths, dtype=dt)
+        m0 = sim.mass()
+        sim.step(1000)
+        h = sim.h().double().cpu().numpy()
+        out[dt]["rel_linf_h_vs_oracle_256_1000"] = float(np.abs(h - ho).max() / np.abs(ho).max())
+        out[dt]["mass_rel_drift_256_1000"] = abs(sim.mass() - m0) / m0
+        sim.close()
+    out["speedup_f16_over_f32"] = out["f16"]["mlups"] / out["f32"]["mlups"]
+    out["speedup_bf16_over_f32"] = out["bf16"]["mlups"] / out["f32"]["mlups"]
+    return out
+
+
+def adjoint_cost(n: int = 512, nsteps: int = 20000):
+    """Cost of one gradient of the inverse-design loss (checkpointed forward +
+    backward with the hand-written adjoint) in units of a plain forward run,
+    FP32, on the inverse-design workload (n^2, T = nsteps, sqrt(T)
+    checkpoints)."""
+    import torch
+    from paper_1810_07642_gb300 import inputs
+    from paper_1810_07642_gb300.adjoint import evolve
+    from paper_1810_07642_gb300.film import ThinFilm
+    h0, th, tgt, p = inputs.inverse_design(n, seed=0)
+    sim = ThinFilm(p, h0, th)
+    sim.step(100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(nsteps)
+    sim.h()
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    sim.close()
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float32, device="cuda")
+    tg = torch.tensor(tgt, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = 0.5 * ((evolve(theta, hh, p, nsteps) - tg) ** 2).sum()
+    torch.cuda.synchronize()
+    t_tape = time.perf_counter() - t0
+    loss.backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    return {"workload": f"inverse design {n}x{n}, T={nsteps}, checkpoints every "
+                        f"{int(math.ceil(math.sqrt(nsteps)))} steps, FP32",
+            "forward_s": t_fwd, "gradient_s": t_grad,
+            "gradient_over_forward": t_grad / t_fwd,
+            "backward_over_forward": (t_grad - t_tape) / t_fwd}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
     2048 x R periodic band of the workload, R sized to fit a few minutes."""
@@ -306,6 +382,10 @@ def run_tflbm(args):
         return 0
     cpu = oracle_cpu_baseline() if world == 1 else None
     clocks = clk.summary()
+    extras = {}
+    if world == 1 and not args.skip_extras:
+        extras["storage"] = storage_variants()
+        extras["adjoint"] = adjoint_cost()
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -327,6 +407,9 @@ def run_tflbm(args):
         "check_status": status,
         "context": {"paper_gtx1080ti_fp64_2048": 404.7},
     }
+    line.update(extras)
+    if "adjoint" in extras:
+        line["adjoint_forward_cost_ratio"] = extras["adjoint"]["gradient_over_forward"]
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -339,6 +422,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="tflbm", choices=["tflbm", "reference"])
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the 16-bit storage and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -172,6 +172,38 @@ int64_t tf_lbm_time(const tf_lbm_handle* H);
 int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out);
 int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse-mode derivative of the step (not in the paper; the method's own
+ * equations differentiated exactly, Eqs. LBE, equilibria, force, pfilm,
+ * disjoiningP, forcefric, alphafric, derivative, n_laplace).  All arrays are
+ * device memory of the handle's compute type (double for TF_LBM_F64, float
+ * otherwise); population arrays are post-streaming, [9][ny][nx].  With
+ * 16-bit storage the derivative is the FP32 scheme's, evaluated on the
+ * stored trajectory. */
+
+/* a_t = dL/df(t) from a_next = dL/df(t+1) for one step taken from the
+ * post-streaming state f_t; adds dL/dkappa of the step to grad_kappa
+ * ([ny][nx], accumulated).  a_t must not alias a_next.  Uses 10 fields of
+ * handle-owned scratch (allocated on first use). */
+int tf_lbm_adjoint_step(tf_lbm_handle* H, const void* f_t, const void* a_next, void* a_t,
+                        void* grad_kappa, void* stream);
+
+/* Gradient tape over nsteps steps with checkpoint-recompute: a copy of the
+ * state every `every` steps (<= 0: ceil(sqrt(nsteps))).  h0 and theta
+ * (device [ny][nx], theta NULL = params->theta_uniform) must be the ones the
+ * handle was created from; they are copied. */
+typedef struct tf_lbm_tape tf_lbm_tape;
+int tf_lbm_tape_create(tf_lbm_handle* H, const void* h0, const void* theta, int64_t nsteps,
+                       int32_t every, tf_lbm_tape** out);
+/* Advance the handle by nsteps, storing the checkpoints. */
+int tf_lbm_tape_forward(tf_lbm_tape* tape, void* stream);
+/* Given grad_h = dL/dh at the final time ([ny][nx]), write dL/dtheta and
+ * dL/dh0 (each [ny][nx], or NULL to skip).  Recomputes each segment from its
+ * checkpoint; the handle ends at the final state again. */
+int tf_lbm_tape_backward(tf_lbm_tape* tape, const void* grad_h, void* grad_theta, void* grad_h0,
+                         void* stream);
+void tf_lbm_tape_destroy(tf_lbm_tape* tape);
+
 /* Largest n accepted by tf_lbm_sum_noalloc: 4096 blocks of 16384 elements. */
 #define TF_LBM_NOALLOC_MAX_ELEMS 67108864LL
 

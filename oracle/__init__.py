@@ -254,7 +254,7 @@ def dkappa_dtheta(cfg: Config, theta) -> np.ndarray:
     return np.sin(np.asarray(theta, np.float64)) * c
 
 
-def gradient(cfg: Config, h0: np.ndarray, theta, nsteps: int, seed):
+def loss_gradient(cfg: Config, h0: np.ndarray, theta, nsteps: int, seed):
     """Reverse-mode gradient of a loss of the final post-streaming state.
 
     seed(f_T) -> (L, dL/df_T).  Keeps every intermediate state (small cases

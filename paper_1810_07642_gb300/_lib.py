@@ -21,7 +21,8 @@ EXPORTED = [
     "tf_lbm_init", "tf_lbm_step", "tf_lbm_moments", "tf_lbm_pressure_force", "tf_lbm_mass",
     "tf_lbm_check", "tf_lbm_get_state", "tf_lbm_set_state", "tf_lbm_time", "tf_lbm_get_launch",
     "tf_lbm_set_launch", "tf_lbm_destroy", "tf_lbm_last_error", "tf_lbm_version",
-    "tf_lbm_sum_noalloc",
+    "tf_lbm_sum_noalloc", "tf_lbm_adjoint_step", "tf_lbm_tape_create", "tf_lbm_tape_forward",
+    "tf_lbm_tape_backward", "tf_lbm_tape_destroy",
 ]
 TF_LBM_NOALLOC_MAX_ELEMS = 67108864
 
@@ -86,6 +87,12 @@ def lib():
     L.tf_lbm_last_error.restype = ctypes.c_char_p
     L.tf_lbm_version.restype = i32
     L.tf_lbm_sum_noalloc.argtypes = [_VP, i64, _VP, _VP]
+    L.tf_lbm_adjoint_step.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+    L.tf_lbm_tape_create.argtypes = [_VP, _VP, _VP, i64, i32, ctypes.POINTER(_VP)]
+    L.tf_lbm_tape_forward.argtypes = [_VP, _VP]
+    L.tf_lbm_tape_backward.argtypes = [_VP, _VP, _VP, _VP, _VP]
+    L.tf_lbm_tape_destroy.argtypes = [_VP]
+    L.tf_lbm_tape_destroy.restype = None
     _lib = L
     return L
 
@@ -173,3 +180,30 @@ def tf_lbm_sum_noalloc(x: int, n: int, out: int, stream: int = 0) -> None:
     """Compensated sum of n device doubles at x into the device double at out,
     allocating nothing (for callers that may not allocate device memory)."""
     _check(lib().tf_lbm_sum_noalloc(_VP(x), int(n), _VP(out), _VP(stream)), None)
+
+
+def tf_lbm_adjoint_step(handle: int, f_t: int, a_next: int, a_t: int, grad_kappa: int,
+                        stream: int = 0) -> None:
+    _check(lib().tf_lbm_adjoint_step(_VP(handle), _VP(f_t), _VP(a_next), _VP(a_t),
+                                     _VP(grad_kappa), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_tape_create(handle: int, h0: int, theta: int | None, nsteps: int, every: int = 0) -> int:
+    t = _VP()
+    _check(lib().tf_lbm_tape_create(_VP(handle), _VP(h0), _VP(theta or 0), int(nsteps), int(every),
+                                    ctypes.byref(t)), _VP(handle))
+    return t.value
+
+
+def tf_lbm_tape_forward(handle: int, tape: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_tape_forward(_VP(tape), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_tape_backward(handle: int, tape: int, grad_h: int, grad_theta: int | None,
+                         grad_h0: int | None, stream: int = 0) -> None:
+    _check(lib().tf_lbm_tape_backward(_VP(tape), _VP(grad_h), _VP(grad_theta or 0),
+                                      _VP(grad_h0 or 0), _VP(stream)), _VP(handle))
+
+
+def tf_lbm_tape_destroy(tape: int) -> None:
+    lib().tf_lbm_tape_destroy(_VP(tape))

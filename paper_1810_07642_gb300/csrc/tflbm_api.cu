@@ -10,36 +10,9 @@
 #include <string>
 
 #include "../../include/tflbm.h"
-#include "tflbm_internal.h"
+#include "tflbm_handle.h"
 
 using namespace tflbm;
-
-struct tf_lbm_handle {
-    tf_lbm_params p;
-    int device = 0;
-    size_t esize = 4;          // bytes of the compute type (plane 0, fields)
-    size_t msize = 4;          // bytes of one stored moving population
-    bool dbl = false;          // compute type is double
-    StoreDesc desc{};          // storage encoding (for the auxiliary kernels)
-    Geom G{};
-    void* buf[2] = {nullptr, nullptr};
-    int cur = 0;               // buf[cur] holds the post-collision populations of step t-1
-    void* kappa = nullptr;     // [ny][nx] or null (uniform)
-    double kappa_u = 0.0;
-    double href = 0.0;         // reference height (exactly representable in the storage type)
-    double* partials = nullptr;
-    double* result = nullptr;
-    int nmass = 0;
-    int* flag = nullptr;
-    int* status = nullptr;     // device word kernels set (kStatusTimeout)
-    void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
-    int64_t time = 0;
-    Shape shape{128, 64, kPipeTma};
-    int graph_chunk = 0;
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    std::string err;
-};
 
 namespace {
 
@@ -85,39 +58,6 @@ int check_dev_ptr(tf_lbm_handle* H, const void* ptr, const char* name, bool allo
     if (a.type == cudaMemoryTypeDevice && a.device != dev)
         return fail(H, TF_LBM_ERR_ARG, std::string(name) + " lives on another device");
     return TF_LBM_OK;
-}
-
-template <typename T>
-Consts<T> make_consts(const tf_lbm_handle* H)
-{
-    Consts<T> C;
-    C.gamma = T(H->p.gamma);
-    C.g = T(H->p.g);
-    C.delta = T(H->p.delta);
-    C.hstar = T(H->p.hstar);
-    C.nu6 = T(6.0 * (H->p.tau - 0.5) / 3.0);
-    C.omega = T(1.0 / H->p.tau);
-    C.gx = T(H->p.gx_body);
-    C.gy = T(H->p.gy_body);
-    C.kappa_u = T(H->kappa_u);
-    C.pi_sgn = T(H->p.pi_sign);
-    C.href = T(H->href);
-    C.mscale = T(H->desc.mscale);
-    C.minv = T(H->desc.minv);
-    C.r_axis = T(H->desc.r_axis);
-    C.r_diag = T(H->desc.r_diag);
-    C.n_exp = H->p.n_exp;
-    C.m_exp = H->p.m_exp;
-    C.status = H->status;
-    return C;
-}
-
-cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
-{
-    const Consts<float> c32 = make_consts<float>(H);
-    const Consts<double> c64 = make_consts<double>(H);
-    return launch_step(H->desc.store, H->buf[from], H->buf[from ^ 1], H->kappa, H->G, &c32, &c64,
-                       H->shape, st);
 }
 
 void drop_graphs(tf_lbm_handle* H)
@@ -199,6 +139,45 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 namespace tflbm {
 // Message for tf_lbm_last_error(NULL) from entry points without a handle.
 void set_thread_error(const std::string& msg) { g_init_err = msg; }
+
+int handle_fail(tf_lbm_handle* H, int code, const std::string& msg) { return fail(H, code, msg); }
+int handle_cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what) { return cuda_fail(H, e, what); }
+
+template <typename T>
+Consts<T> make_consts(const tf_lbm_handle* H)
+{
+    Consts<T> C;
+    C.gamma = T(H->p.gamma);
+    C.g = T(H->p.g);
+    C.delta = T(H->p.delta);
+    C.hstar = T(H->p.hstar);
+    C.nu6 = T(6.0 * (H->p.tau - 0.5) / 3.0);
+    C.omega = T(1.0 / H->p.tau);
+    C.gx = T(H->p.gx_body);
+    C.gy = T(H->p.gy_body);
+    C.kappa_u = T(H->kappa_u);
+    C.pi_sgn = T(H->p.pi_sign);
+    C.href = T(H->href);
+    C.mscale = T(H->desc.mscale);
+    C.minv = T(H->desc.minv);
+    C.r_axis = T(H->desc.r_axis);
+    C.r_diag = T(H->desc.r_diag);
+    C.n_exp = H->p.n_exp;
+    C.m_exp = H->p.m_exp;
+    C.status = H->status;
+    return C;
+}
+
+cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
+{
+    const Consts<float> c32 = make_consts<float>(H);
+    const Consts<double> c64 = make_consts<double>(H);
+    return launch_step(H->desc.store, H->buf[from], H->buf[from ^ 1], H->kappa, H->G, &c32, &c64,
+                       H->shape, st);
+}
+
+template Consts<float> make_consts<float>(const tf_lbm_handle*);
+template Consts<double> make_consts<double>(const tf_lbm_handle*);
 }  // namespace tflbm
 
 static_assert(kStatusTimeout == TF_LBM_STATUS_TIMEOUT, "status bits out of sync");
@@ -465,6 +444,7 @@ void tf_lbm_destroy(tf_lbm_handle* H)
     if (H->partials) cudaFree(H->partials);
     if (H->flag) cudaFree(H->flag);
     if (H->diag) cudaFree(H->diag);
+    if (H->adj) cudaFree(H->adj);
     delete H;
 }
 

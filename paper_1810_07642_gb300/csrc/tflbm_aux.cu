@@ -334,6 +334,20 @@ __global__ void k_get_state(Pops<T, SM> P, double* out, Geom G)
     }
 }
 
+// Post-streaming populations in the compute type, [9][ny][nx] (adjoint input).
+template <typename T, typename SM>
+__global__ void k_export_state(Pops<T, SM> P, T* out, Geom G)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= G.nx) return;
+    T v[9];
+    pull_at(P, G, x, y, v);
+    const long long n = (long long)G.nx * G.ny, i = (long long)y * G.nx + x;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) out[l * n + i] = v[l];
+}
+
 template <typename T, typename SM>
 __global__ void k_set_state(Pops<T, SM> P, const double* __restrict__ in, Geom G)
 {
@@ -401,6 +415,13 @@ cudaError_t get_t(const StoreDesc& D, const void* f, double* out, const Geom& G,
 }
 
 template <typename T, typename SM>
+cudaError_t export_t(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st)
+{
+    k_export_state<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), (T*)out, G);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
 cudaError_t set_t(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st)
 {
     k_set_state<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), in, G);
@@ -464,6 +485,11 @@ cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* fla
 cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st)
 {
     TFLBM_DISPATCH(D, (get_t<T, SM>(D, f, out, G, st)))
+}
+
+cudaError_t aux_export_state(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st)
+{
+    TFLBM_DISPATCH(D, (export_t<T, SM>(D, f, out, G, st)))
 }
 
 cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st)

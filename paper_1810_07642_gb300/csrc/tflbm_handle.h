@@ -1,0 +1,55 @@
+// Internal definition of the opaque tf_lbm_handle, shared by the C-ABI
+// translation units (tflbm_api.cu, tflbm_adjoint.cu).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tflbm.h"
+#include "tflbm_internal.h"
+
+using namespace tflbm;
+
+struct tf_lbm_handle {
+    tf_lbm_params p;
+    int device = 0;
+    size_t esize = 4;          // bytes of the compute type (plane 0, fields)
+    size_t msize = 4;          // bytes of one stored moving population
+    bool dbl = false;          // compute type is double
+    StoreDesc desc{};          // storage encoding (for the auxiliary kernels)
+    Geom G{};
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;               // buf[cur] holds the post-collision populations of step t-1
+    void* kappa = nullptr;     // [ny][nx] or null (uniform)
+    double kappa_u = 0.0;
+    double href = 0.0;         // reference height (exactly representable in the storage type)
+    double* partials = nullptr;
+    double* result = nullptr;
+    int nmass = 0;
+    int* flag = nullptr;
+    int* status = nullptr;     // device word kernels set (kStatusTimeout)
+    void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
+    int64_t time = 0;
+    Shape shape{128, 64, kPipeTma};
+    int graph_chunk = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::string err;
+    void* adj = nullptr;       // adjoint scratch (lazy): 10 fields of the compute type
+};
+
+
+namespace tflbm {
+// Per-run step constants of a handle, in the compute type T.
+template <typename T>
+Consts<T> make_consts(const tf_lbm_handle* H);
+// Launch one fused step from buf[from] into buf[from ^ 1].
+cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st);
+// Record an error message on H (or for the calling thread when H is null).
+int handle_fail(tf_lbm_handle* H, int code, const std::string& msg);
+int handle_cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what);
+// Adjoint of one step (tflbm_adjoint.cu).
+cudaError_t adjoint_step_dispatch(tf_lbm_handle* H, const void* f, const void* a_next, void* a,
+                                  void* grad_kappa, cudaStream_t st);
+}  // namespace tflbm

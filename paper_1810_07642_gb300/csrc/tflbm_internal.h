@@ -90,6 +90,8 @@ cudaError_t aux_mass(const StoreDesc& D, const void* f, const Geom& G, double* p
 cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st);
 cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st);
+// post-streaming populations in the compute type, [9][ny][nx]
+cudaError_t aux_export_state(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
                       double hstar, cudaStream_t st);
 cudaError_t aux_sum(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,

@@ -60,7 +60,8 @@ class ThinFilm:
         st = _stream_ptr(stream)
         self.handle = L.tf_lbm_init(self.cparams, h0.data_ptr(),
                                     th.data_ptr() if th is not None else None, st)
-        # keep inputs alive until the init kernels have consumed them
+        # the device copies of h0 and theta (kept for gradient tapes)
+        self.h0_dev, self.theta_dev = h0, th
         self._keep = (h0, th)
         self._st = st
 

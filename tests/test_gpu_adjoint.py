@@ -1,0 +1,149 @@
+"""GPU adjoint (tf_lbm_adjoint_step, gradient tape, autograd Function)
+against the FP64 oracle adjoint and against central finite differences.
+
+Tolerances: one adjoint step in FP64 agrees with the oracle to 1e-10
+relative (summation order only); in FP32 to 1e-4 of the largest entry (the
+adjoint mixes terms of very different size, e.g. 1/h^2 in the equilibrium
+derivatives).  Whole gradients through the tape in FP64 agree with the oracle
+driver to 1e-9 and with central differences of the GPU FP64 forward to 1e-4,
+the bound the inverse-design workload asks for.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1810_07642_gb300 import _lib as L
+from paper_1810_07642_gb300 import inputs
+from paper_1810_07642_gb300.adjoint import evolve
+from paper_1810_07642_gb300.film import ThinFilm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    from paper_1810_07642_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def cfg_of(p, **over):
+    d = {k: v for k, v in p.items() if k in O.Config.__dataclass_fields__}
+    d.update(over)
+    return O.Config(**d)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-4)])
+@pytest.mark.parametrize("case", [dict(tau=1.0, g=0.0), dict(tau=0.8, g=2e-3, gx_body=1e-4, delta=0.5),
+                                  dict(tau=1.2, g=-1e-3, pi_sign=-1, n_exp=9, m_exp=3)])
+def test_adjoint_step_matches_oracle(dtype, tol, case):
+    nx, ny = 37, 29
+    h0, th, p = inputs.small_random(nx, ny, seed=3, amp=0.2)
+    p.update(case)
+    cfg = cfg_of(p)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    O.step(cfg, kap, f, 7)
+    a_next = np.random.default_rng(1).standard_normal((9, ny, nx))
+    gk_o = np.zeros((ny, nx))
+    a_o = O.adjoint_step(cfg, kap, f, a_next, gk_o)
+
+    sim = ThinFilm(p, h0, th, dtype=dtype)
+    td = sim.tdtype
+    ft = torch.as_tensor(f, dtype=td, device="cuda").contiguous()
+    an = torch.as_tensor(a_next, dtype=td, device="cuda").contiguous()
+    at = torch.empty_like(an)
+    gk = torch.zeros((ny, nx), dtype=td, device="cuda")
+    L.tf_lbm_adjoint_step(sim.handle, ft.data_ptr(), an.data_ptr(), at.data_ptr(), gk.data_ptr(),
+                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    a_g = at.double().cpu().numpy()
+    gk_g = gk.double().cpu().numpy()
+    assert np.abs(a_g - a_o).max() <= tol * np.abs(a_o).max()
+    assert np.abs(gk_g - gk_o).max() <= tol * np.abs(gk_o).max()
+
+
+def _oracle_grads(p, h0, th, T, tgt):
+    cfg = cfg_of(p)
+
+    def seed(f):
+        h = f.sum(0)
+        return 0.5 * float(((h - tgt) ** 2).sum()), np.broadcast_to(h - tgt, f.shape).copy()
+
+    return O.loss_gradient(cfg, h0, th, T, seed)
+
+
+@pytest.mark.parametrize("every", [7, 0, 100])
+def test_tape_gradient_matches_oracle_fp64(every):
+    """Checkpoint segments of 7 (with a partial last one), sqrt(T), and one
+    segment for the whole run all give the oracle's gradient."""
+    h0, th, p = inputs.small_random(40, 32, seed=5, amp=0.1)
+    p.update(tau=0.9, g=1e-3, delta=0.8)
+    T = 30
+    tgt = np.random.default_rng(2).uniform(0.9, 1.1, h0.shape)
+    L_o, gth_o, gh0_o, _ = _oracle_grads(p, h0, th, T, tgt)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float64, device="cuda", requires_grad=True)
+    h_t = evolve(theta, hh, p, T, dtype="f64", every=every)
+    tg = torch.tensor(tgt, device="cuda")
+    loss = 0.5 * ((h_t - tg) ** 2).sum()
+    loss.backward()
+    assert abs(loss.item() - L_o) <= 1e-11 * abs(L_o)
+    gth = theta.grad.cpu().numpy()
+    gh0 = hh.grad.cpu().numpy()
+    assert np.abs(gth - gth_o).max() <= 1e-9 * np.abs(gth_o).max()
+    assert np.abs(gh0 - gh0_o).max() <= 1e-9 * np.abs(gh0_o).max()
+
+
+def test_gradient_matches_central_differences_inverse_design():
+    """The inverse-design workload shape (noisy film, noisy theta, 8-drop
+    target, L2 loss), reduced to 128^2 and 300 steps: dL/dtheta from the FP64
+    tape against central differences (step 1e-4 rad) of the GPU FP64 forward
+    on 16 random theta pixels, within 1e-4 relative."""
+    h0, th, tgt, p = inputs.inverse_design(128, seed=1)
+    T = 300
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float64, device="cuda")
+    tg = torch.tensor(tgt, device="cuda")
+    loss = 0.5 * ((evolve(theta, hh, p, T, dtype="f64") - tg) ** 2).sum()
+    loss.backward()
+    g = theta.grad.cpu().numpy()
+
+    def L_of(th_):
+        sim = ThinFilm(p, h0, th_, dtype="f64")
+        sim.step(T)
+        h = sim.h()
+        return 0.5 * float(((h - tg) ** 2).sum().item())
+
+    rng = np.random.default_rng(7)
+    eps = 1e-4
+    floor = 1e-3 * np.abs(g).max()  # pixels whose gradient is ~0 are judged against this
+    worst = 0.0
+    for _ in range(16):
+        y, x = int(rng.integers(0, 128)), int(rng.integers(0, 128))
+        tp, tm = th.copy(), th.copy()
+        tp[y, x] += eps
+        tm[y, x] -= eps
+        fd = (L_of(tp) - L_of(tm)) / (2 * eps)
+        worst = max(worst, abs(fd - g[y, x]) / max(abs(g[y, x]), floor))
+    assert worst <= 1e-4, worst
+
+
+def test_fp32_gradient_close_to_fp64():
+    h0, th, tgt, p = inputs.inverse_design(64, seed=2)
+    T = 200
+    grads = {}
+    for dt in ("f32", "f64"):
+        theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+        hh = torch.tensor(h0, dtype=torch.float64, device="cuda", requires_grad=True)
+        tg = torch.tensor(tgt, device="cuda")
+        loss = 0.5 * ((evolve(theta, hh, p, T, dtype=dt).double() - tg) ** 2).sum()
+        loss.backward()
+        grads[dt] = (theta.grad.cpu().numpy(), hh.grad.cpu().numpy())
+    for k in range(2):
+        a, b = grads["f32"][k], grads["f64"][k]
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max()

@@ -38,7 +38,7 @@ def test_adjoint_matches_central_differences(case):
     cfg = cfg_of(p)
     rng = np.random.default_rng(case)
     r = rng.standard_normal((9, ny, nx))  # a random linear functional of f(T)
-    L, gth, gh0, gk = O.gradient(cfg, h0, th, T, lambda f: (float((r * f).sum()), r.copy()))
+    L, gth, gh0, gk = O.loss_gradient(cfg, h0, th, T, lambda f: (float((r * f).sum()), r.copy()))
     assert abs(L - _forward_loss(cfg, h0, th, T, r)) < 1e-12 * abs(L)
     scale = max(np.abs(gth).max(), np.abs(gh0).max())
     for _ in range(6):
@@ -69,7 +69,7 @@ def test_adjoint_of_height_loss_on_drop():
         return 0.5 * float(((h - tgt) ** 2).sum()), np.broadcast_to(h - tgt, f.shape).copy()
 
     T = 8
-    L, gth, gh0, _ = O.gradient(cfg, h0, th, T, seed)
+    L, gth, gh0, _ = O.loss_gradient(cfg, h0, th, T, seed)
 
     def loss(h0_, th_):
         f = O.init(cfg, h0_)
