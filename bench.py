@@ -232,6 +232,9 @@ def adjoint_cost(n: int = 512, nsteps: int = 20000):
     theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
     hh = torch.tensor(h0, dtype=torch.float32, device="cuda")
     tg = torch.tensor(tgt, dtype=torch.float32, device="cuda")
+    # warm-up: first use of the adjoint kernels and graph capture paths
+    (0.5 * ((evolve(theta, hh, p, 300) - tg) ** 2).sum()).backward()
+    theta.grad = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     loss = 0.5 * ((evolve(theta, hh, p, nsteps) - tg) ** 2).sum()

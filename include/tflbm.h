@@ -204,6 +204,90 @@ int tf_lbm_tape_backward(tf_lbm_tape* tape, const void* grad_h, void* grad_theta
                          void* stream);
 void tf_lbm_tape_destroy(tf_lbm_tape* tape);
 
+/* ---------------------------------------------------------- autotuning
+ * Time candidate launch shapes of the fused step on the handle's own state
+ * and keep the fastest.  Each candidate runs 2 untimed and `trial_steps`
+ * timed steps (rounded up to even; <= 0 means 16), timed with CUDA events on
+ * `stream`.  Candidates: block_x in {64, 128, 256}, both pipelines where the
+ * bulk-copy one applies, and band heights around the one that fills a single
+ * wave of resident CTAs.  The state is copied aside first (one population
+ * buffer of device memory, freed before return) and put back after, so f
+ * and tf_lbm_time are as before the call.  The graph chunk is kept.
+ * Synchronises `stream`.  best (host, may be NULL) receives the shape now in
+ * use. */
+int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void* stream);
+
+/* -------------------------------------------------------- diagnostics
+ * Film diagnostics of the current state, computed on the device (Section
+ * III: the drop's contact radius from its wetted area, its apex height, its
+ * sliding velocity U from momentum over the wetted nodes, Ca = nu U / gamma
+ * with rho = 1).  The wetted nodes are those with h > h_wet.  Every sum is
+ * taken in double precision with compensated summation. */
+typedef struct tf_lbm_diag {
+    double mass;      /* sum of h over the lattice                          */
+    double wet_mass;  /* sum of h over the wetted nodes                     */
+    double wet_jx;    /* sum of j_x = sum_l c_lx f_l over the wetted nodes  */
+    double wet_jy;    /* sum of j_y over the wetted nodes                   */
+    double wet_area;  /* number of wetted nodes                             */
+    double h_max;     /* largest h                                          */
+} tf_lbm_diag;
+/* out: device pointer to one tf_lbm_diag (six doubles), written
+ * asynchronously on `stream` (no host synchronisation).  Uses a small
+ * handle-owned scratch allocated on first use. */
+int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, void* out, void* stream);
+
+/* --------------------------------------------------------------- batches
+ * Many independent simulations of uneven sizes (a parameter sweep) advanced
+ * together: each step is ONE launch over a table of work items, (domain,
+ * column strip, row band), and tf_lbm_batch_step replays CUDA graphs of
+ * graph_chunk such launches.  The batch borrows the handles: they stay
+ * owned by the caller, must outlive the batch and must all have the same
+ * dtype; the per-handle calls (moments, mass, check, diagnostics, state
+ * import and export) work between batch steps, as does tf_lbm_step on a
+ * single handle.  Handles with a theta field and handles without one may be
+ * mixed (the batch then keeps a filled kappa field for the uniform ones).
+ * When some handles have tau == 1 and others not, all take the general-tau
+ * kernel, so those with tau == 1 match their single-handle results to
+ * rounding rather than bit for bit. */
+typedef struct tf_lbm_batch tf_lbm_batch;
+
+/* Launch shape of a batch.
+ *   block_x, rows: as in tf_lbm_launch, common to all domains (a domain of
+ *            ny rows is cut into ceil(ny / rows) near-equal bands);
+ *   graph_chunk: steps per captured CUDA graph (0 or even, <= 4096);
+ *   queue:   0 = one CTA per work item; 1 = a persistent grid of one wave of
+ *            resident CTAs, each taking items from an atomic counter until
+ *            none are left. */
+typedef struct tf_lbm_batch_launch {
+    int32_t block_x;
+    int32_t rows;
+    int32_t graph_chunk;
+    int32_t queue;
+} tf_lbm_batch_launch;
+
+/* Create a batch of `count` >= 1 handles (host array, copied).  ARG error
+ * on NULL handles, a repeated handle or mixed dtypes. */
+int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32_t count, void* stream);
+/* Advance every handle of the batch by nsteps >= 0. */
+int tf_lbm_batch_step(tf_lbm_batch* B, int64_t nsteps, void* stream);
+int tf_lbm_batch_get_launch(const tf_lbm_batch* B, tf_lbm_batch_launch* out);
+int tf_lbm_batch_set_launch(tf_lbm_batch* B, const tf_lbm_batch_launch* in);
+/* As tf_lbm_tune, over block_x, rows and queue, for the whole batch (every
+ * handle's state copied aside and put back). */
+int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch* best, void* stream);
+/* tf_lbm_diagnostics of every handle in two launches: out is a device array
+ * of `count` tf_lbm_diag, in the order of the handles. */
+int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, void* out, void* stream);
+/* Number of work items of one batched step (= CTAs without the queue). */
+int32_t tf_lbm_batch_items(const tf_lbm_batch* B);
+/* Waits for the batch's device work and frees what it owns (not the
+ * handles).  NULL ok. */
+void tf_lbm_batch_destroy(tf_lbm_batch* B);
+/* Message of the last failed call on B (B != NULL), or of the last failed
+ * tf_lbm_batch_create on this thread (B == NULL, same as
+ * tf_lbm_last_error(NULL)). */
+const char* tf_lbm_batch_last_error(const tf_lbm_batch* B);
+
 /* Largest n accepted by tf_lbm_sum_noalloc: 4096 blocks of 16384 elements. */
 #define TF_LBM_NOALLOC_MAX_ELEMS 67108864LL
 

@@ -22,8 +22,13 @@ EXPORTED = [
     "tf_lbm_check", "tf_lbm_get_state", "tf_lbm_set_state", "tf_lbm_time", "tf_lbm_get_launch",
     "tf_lbm_set_launch", "tf_lbm_destroy", "tf_lbm_last_error", "tf_lbm_version",
     "tf_lbm_sum_noalloc", "tf_lbm_adjoint_step", "tf_lbm_tape_create", "tf_lbm_tape_forward",
-    "tf_lbm_tape_backward", "tf_lbm_tape_destroy",
+    "tf_lbm_tape_backward", "tf_lbm_tape_destroy", "tf_lbm_tune", "tf_lbm_diagnostics",
+    "tf_lbm_batch_create", "tf_lbm_batch_step", "tf_lbm_batch_get_launch", "tf_lbm_batch_set_launch",
+    "tf_lbm_batch_tune", "tf_lbm_batch_diagnostics", "tf_lbm_batch_items", "tf_lbm_batch_destroy",
+    "tf_lbm_batch_last_error",
 ]
+# fields of tf_lbm_diag, in order
+DIAG_FIELDS = ("mass", "wet_mass", "wet_jx", "wet_jy", "wet_area", "h_max")
 TF_LBM_NOALLOC_MAX_ELEMS = 67108864
 
 
@@ -48,6 +53,12 @@ class Launch(ctypes.Structure):
     """Mirror of tf_lbm_launch."""
     _fields_ = [("block_x", ctypes.c_int32), ("rows", ctypes.c_int32),
                 ("graph_chunk", ctypes.c_int32), ("pipeline", ctypes.c_int32)]
+
+
+class BatchLaunch(ctypes.Structure):
+    """Mirror of tf_lbm_batch_launch."""
+    _fields_ = [("block_x", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("graph_chunk", ctypes.c_int32), ("queue", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,6 +104,20 @@ def lib():
     L.tf_lbm_tape_backward.argtypes = [_VP, _VP, _VP, _VP, _VP]
     L.tf_lbm_tape_destroy.argtypes = [_VP]
     L.tf_lbm_tape_destroy.restype = None
+    L.tf_lbm_tune.argtypes = [_VP, i32, ctypes.POINTER(Launch), _VP]
+    L.tf_lbm_diagnostics.argtypes = [_VP, ctypes.c_double, _VP, _VP]
+    L.tf_lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(_VP), i32, _VP]
+    L.tf_lbm_batch_step.argtypes = [_VP, i64, _VP]
+    L.tf_lbm_batch_get_launch.argtypes = [_VP, ctypes.POINTER(BatchLaunch)]
+    L.tf_lbm_batch_set_launch.argtypes = [_VP, ctypes.POINTER(BatchLaunch)]
+    L.tf_lbm_batch_tune.argtypes = [_VP, i32, ctypes.POINTER(BatchLaunch), _VP]
+    L.tf_lbm_batch_diagnostics.argtypes = [_VP, ctypes.c_double, _VP, _VP]
+    L.tf_lbm_batch_items.argtypes = [_VP]
+    L.tf_lbm_batch_items.restype = i32
+    L.tf_lbm_batch_destroy.argtypes = [_VP]
+    L.tf_lbm_batch_destroy.restype = None
+    L.tf_lbm_batch_last_error.argtypes = [_VP]
+    L.tf_lbm_batch_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -207,3 +232,64 @@ def tf_lbm_tape_backward(handle: int, tape: int, grad_h: int, grad_theta: int | 
 
 def tf_lbm_tape_destroy(tape: int) -> None:
     lib().tf_lbm_tape_destroy(_VP(tape))
+
+
+def tf_lbm_tune(handle: int, trial_steps: int = 16, stream: int = 0) -> Launch:
+    out = Launch()
+    _check(lib().tf_lbm_tune(_VP(handle), int(trial_steps), ctypes.byref(out), _VP(stream)), _VP(handle))
+    return out
+
+
+def tf_lbm_diagnostics(handle: int, h_wet: float, out: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_diagnostics(_VP(handle), float(h_wet), _VP(out), _VP(stream)), _VP(handle))
+
+
+def _bcheck(rc: int, batch=None):
+    if rc != TF_LBM_OK:
+        msg = lib().tf_lbm_batch_last_error(batch).decode(errors="replace")
+        raise TfLbmError(rc, msg)
+
+
+def tf_lbm_batch_create(handles, stream: int = 0) -> int:
+    arr = (_VP * len(handles))(*[_VP(h) for h in handles])
+    b = _VP()
+    _bcheck(lib().tf_lbm_batch_create(ctypes.byref(b), arr, len(handles), _VP(stream)), None)
+    return b.value
+
+
+def tf_lbm_batch_step(batch: int, nsteps: int, stream: int = 0) -> None:
+    _bcheck(lib().tf_lbm_batch_step(_VP(batch), int(nsteps), _VP(stream)), _VP(batch))
+
+
+def tf_lbm_batch_get_launch(batch: int) -> BatchLaunch:
+    out = BatchLaunch()
+    _bcheck(lib().tf_lbm_batch_get_launch(_VP(batch), ctypes.byref(out)), _VP(batch))
+    return out
+
+
+def tf_lbm_batch_set_launch(batch: int, block_x: int, rows: int, graph_chunk: int, queue: int = 0) -> None:
+    L = BatchLaunch(block_x, rows, graph_chunk, queue)
+    _bcheck(lib().tf_lbm_batch_set_launch(_VP(batch), ctypes.byref(L)), _VP(batch))
+
+
+def tf_lbm_batch_tune(batch: int, trial_steps: int = 16, stream: int = 0) -> BatchLaunch:
+    out = BatchLaunch()
+    _bcheck(lib().tf_lbm_batch_tune(_VP(batch), int(trial_steps), ctypes.byref(out), _VP(stream)),
+            _VP(batch))
+    return out
+
+
+def tf_lbm_batch_diagnostics(batch: int, h_wet: float, out: int, stream: int = 0) -> None:
+    _bcheck(lib().tf_lbm_batch_diagnostics(_VP(batch), float(h_wet), _VP(out), _VP(stream)), _VP(batch))
+
+
+def tf_lbm_batch_items(batch: int) -> int:
+    return int(lib().tf_lbm_batch_items(_VP(batch)))
+
+
+def tf_lbm_batch_destroy(batch: int) -> None:
+    lib().tf_lbm_batch_destroy(_VP(batch))
+
+
+def tf_lbm_batch_last_error(batch: int | None = None) -> str:
+    return lib().tf_lbm_batch_last_error(_VP(batch or 0)).decode(errors="replace")

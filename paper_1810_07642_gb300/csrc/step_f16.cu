@@ -48,4 +48,11 @@ int blocks_per_sm_narrow(int store, int pipeline, int block_x, bool omega1, bool
     return 0;
 }
 
+cudaError_t launch_batch_narrow(int store, const BatchLaunch& L, cudaStream_t st)
+{
+    if (store == kStoreF16) return launch_batch_typed<__half, float>(L, st);
+    if (store == kStoreBF16) return launch_batch_typed<__nv_bfloat16, float>(L, st);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace tflbm

@@ -8,6 +8,7 @@ cudaError_t launch_step_narrow(int store, const void* fin, void* fout, const voi
                                const Geom& G, const Consts<float>& C, const Shape& S,
                                cudaStream_t st);
 int blocks_per_sm_narrow(int store, int pipeline, int block_x, bool omega1, bool kfield);
+cudaError_t launch_batch_narrow(int store, const BatchLaunch& L, cudaStream_t st);
 
 template <typename SM, typename T>
 static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, const Geom& G,
@@ -52,6 +53,15 @@ int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool k
         }
     }
     return blocks_per_sm_narrow(store, pipeline, block_x, omega1, kfield);
+}
+
+cudaError_t launch_step_batch(int store, const BatchLaunch& L, cudaStream_t st)
+{
+    switch (store) {
+        case kStoreF32: return launch_batch_typed<float, float>(L, st);
+        case kStoreF64: return launch_batch_typed<double, double>(L, st);
+        default: return launch_batch_narrow(store, L, st);
+    }
 }
 
 }  // namespace tflbm

@@ -34,17 +34,30 @@ namespace {
 __device__ __constant__ int aCx[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
 __device__ __constant__ int aCy[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
 
-__device__ __forceinline__ int wrp(int i, int n)
-{
-    i %= n;
-    return i < 0 ? i + n : i;
-}
 
 template <typename T> __device__ __forceinline__ T wgt(int l) { return l == 0 ? T(4.0 / 9.0) : ((l & 1) ? T(1.0 / 9.0) : T(1.0 / 36.0)); }
 
 struct Dims {
     int nx, ny;
     long long n;  // nx * ny
+};
+
+// Wrapped neighbourhood of node (x, y): row offsets of y-1, y, y+1 and
+// columns x-1, x, x+1 (no integer division).
+struct Nbr {
+    long long r[3];
+    int c[3];
+    __device__ __forceinline__ Nbr(int x, int y, const Dims& D)
+    {
+        r[0] = (long long)(y == 0 ? D.ny - 1 : y - 1) * D.nx;
+        r[1] = (long long)y * D.nx;
+        r[2] = (long long)(y + 1 == D.ny ? 0 : y + 1) * D.nx;
+        c[0] = x == 0 ? D.nx - 1 : x - 1;
+        c[1] = x;
+        c[2] = x + 1 == D.nx ? 0 : x + 1;
+    }
+    // index of node (x + dx, y + dy), dx, dy in {-1, 0, 1}
+    __device__ __forceinline__ long long at(int dy, int dx) const { return r[dy + 1] + c[dx + 1]; }
 };
 
 // h, j of the state f at every node
@@ -74,7 +87,8 @@ __global__ void k_adj_pressure(const T* __restrict__ h, const T* __restrict__ ka
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= D.nx) return;
-    auto H = [&](int dy, int dx) { return h[(long long)wrp(y + dy, D.ny) * D.nx + wrp(x + dx, D.nx)]; };
+    const Nbr nb(x, y, D);
+    auto H = [&](int dy, int dx) { return h[nb.at(dy, dx)]; };
     const T axis = H(0, -1) + H(0, 1) + H(-1, 0) + H(1, 0);
     const T diag = H(-1, -1) + H(-1, 1) + H(1, -1) + H(1, 1);
     const T hh = H(0, 0);
@@ -97,7 +111,8 @@ __global__ void k_adj_collide(const T* __restrict__ h, const T* __restrict__ jx,
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= D.nx) return;
     const long long i = (long long)y * D.nx + x;
-    auto Pp = [&](int dy, int dx) { return p[(long long)wrp(y + dy, D.ny) * D.nx + wrp(x + dx, D.nx)]; };
+    const Nbr nb(x, y, D);
+    auto Pp = [&](int dy, int dx) { return p[nb.at(dy, dx)]; };
     // Eq. (derivative) at the node
     const T gpx = (Pp(0, 1) - Pp(0, -1)) / T(3) + (Pp(1, 1) - Pp(1, -1) + Pp(-1, 1) - Pp(-1, -1)) / T(12);
     const T gpy = (Pp(1, 0) - Pp(-1, 0)) / T(3) + (Pp(1, 1) - Pp(-1, 1) + Pp(1, -1) - Pp(-1, -1)) / T(12);
@@ -105,7 +120,7 @@ __global__ void k_adj_collide(const T* __restrict__ h, const T* __restrict__ jx,
     T aFx = 0, aFy = 0, ah = 0, ajx = 0, ajy = 0;
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-        const T m = a_next[l * D.n + (long long)wrp(y + aCy[l], D.ny) * D.nx + wrp(x + aCx[l], D.nx)];
+        const T m = a_next[l * D.n + nb.at(aCy[l], aCx[l])];
         aFx += T(3) * wgt<T>(l) * T(aCx[l]) * m;
         aFy += T(3) * wgt<T>(l) * T(aCy[l]) * m;
         const T am = w * m;
@@ -149,10 +164,11 @@ __global__ void k_adj_pressure_t(const T* __restrict__ agx, const T* __restrict_
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= D.nx) return;
     const long long i = (long long)y * D.nx + x;
+    const Nbr nb(x, y, D);
     T ap = 0;
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-        const long long k = (long long)wrp(y - aCy[l], D.ny) * D.nx + wrp(x - aCx[l], D.nx);
+        const long long k = nb.at(-aCy[l], -aCx[l]);
         ap += T(3) * wgt<T>(l) * (T(aCx[l]) * agx[k] + T(aCy[l]) * agy[k]);
     }
     alap[i] = -C.gamma * ap;
@@ -176,14 +192,15 @@ __global__ void k_adj_out(const T* __restrict__ aH, const T* __restrict__ alap, 
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= D.nx) return;
     const long long i = (long long)y * D.nx + x;
-    auto Ls = [&](int dy, int dx) { return alap[(long long)wrp(y + dy, D.ny) * D.nx + wrp(x + dx, D.nx)]; };
+    const Nbr nb(x, y, D);
+    auto Ls = [&](int dy, int dx) { return alap[nb.at(dy, dx)]; };
     const T axis = Ls(0, -1) + Ls(0, 1) + Ls(-1, 0) + Ls(1, 0);
     const T diag = Ls(-1, -1) + Ls(-1, 1) + Ls(1, -1) + Ls(1, 1);
     const T ah = aH[i] + (T(4) * axis + diag - T(20) * Ls(0, 0)) / T(6);
     const T jx = aJx[i], jy = aJy[i], om = T(1) - C.omega;
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-        const T m = a_next[l * D.n + (long long)wrp(y + aCy[l], D.ny) * D.nx + wrp(x + aCx[l], D.nx)];
+        const T m = a_next[l * D.n + nb.at(aCy[l], aCx[l])];
         a[l * D.n + i] = ah + T(aCx[l]) * jx + T(aCy[l]) * jy + om * m;
     }
 }
@@ -265,6 +282,11 @@ struct tf_lbm_tape {
     void* theta = nullptr;         // copy of theta or null (uniform)
     int64_t t0 = 0;                // handle time when the forward started
     bool forwarded = false;
+    // CUDA graphs of one full segment: recompute (by starting buffer) and
+    // the adjoint chain (by starting adjoint buffer)
+    cudaGraphExec_t g_rec[2] = {nullptr, nullptr};
+    cudaGraphExec_t g_adj[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
 };
 
 namespace {
@@ -277,14 +299,60 @@ int tape_fail(tf_lbm_tape* tp, int code, const char* msg) { return handle_fail(t
         if (e_ != cudaSuccess) return handle_cuda_fail((tp)->H, e_, what);      \
     } while (0)
 
-// one fused step of the handle, tracking its ping-pong buffer and clock
-cudaError_t one_step(tf_lbm_handle* H, cudaStream_t st)
+// Recompute the len states of a segment from the state in buf[from]:
+// export, step, export, ..., export (len exports, len - 1 steps).
+cudaError_t recompute(tf_lbm_tape* tp, int from, int64_t len, cudaStream_t st)
 {
-    cudaError_t e = launch_one_step(H, H->cur, st);
-    if (e == cudaSuccess) {
-        H->cur ^= 1;
-        H->time += 1;
+    tf_lbm_handle* H = tp->H;
+    const size_t sbytes = 9ull * H->G.nx * H->G.ny * H->esize;
+    char* seg = (char*)tp->seg;
+    int cur = from;
+    for (int64_t i = 0; i < len; ++i) {
+        cudaError_t e = aux_export_state(H->desc, H->buf[cur], seg + i * sbytes, H->G, st);
+        if (e == cudaSuccess && i + 1 < len) {
+            e = launch_one_step(H, cur, st);
+            cur ^= 1;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+// Adjoint steps backwards through a segment of len states, starting from the
+// adjoint state in abuf slot `from`.
+cudaError_t adjoint_chain(tf_lbm_tape* tp, int from, int64_t len, cudaStream_t st)
+{
+    tf_lbm_handle* H = tp->H;
+    const size_t sbytes = 9ull * H->G.nx * H->G.ny * H->esize;
+    char* seg = (char*)tp->seg;
+    char* ab = (char*)tp->abuf;
+    int cur = from;
+    for (int64_t i = len - 1; i >= 0; --i) {
+        cudaError_t e = adjoint_step_dispatch(H, seg + i * sbytes, ab + cur * sbytes, ab + (cur ^ 1) * sbytes,
+                                              tp->gk, st);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return cudaSuccess;
+}
+
+// Capture fn into an executable graph (on the tape's own capture stream).
+template <typename Fn>
+cudaError_t capture(tf_lbm_tape* tp, cudaGraphExec_t* out, Fn fn)
+{
+    cudaError_t e;
+    if (!tp->cap && (e = cudaStreamCreateWithFlags(&tp->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(tp->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t fe = fn(tp->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(tp->cap, &g);
+    if (fe != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fe;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
     return e;
 }
 
@@ -327,6 +395,7 @@ int tf_lbm_tape_create(tf_lbm_handle* H, const void* h0, const void* theta, int6
         tf_lbm_tape_destroy(tp);
         return rc;
     };
+    if (!H->adj && (e = cudaMalloc(&H->adj, 10ull * n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc adjoint scratch");
     if ((e = cudaMalloc(&tp->ck, tp->state_bytes * (tp->nck + 1))) != cudaSuccess) return bail(e, "cudaMalloc checkpoints");
     if ((e = cudaMalloc(&tp->seg, 9ull * n * H->esize * (every + 1))) != cudaSuccess) return bail(e, "cudaMalloc segment");
     if ((e = cudaMalloc(&tp->abuf, 18ull * n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc adjoint");
@@ -353,7 +422,8 @@ int tf_lbm_tape_forward(tf_lbm_tape* tp, void* stream)
         TK(tp, cudaMemcpyAsync(ck + c * tp->state_bytes, H->buf[H->cur], tp->state_bytes, cudaMemcpyDeviceToDevice, st),
            "checkpoint copy");
         const int64_t len = (c + 1 == tp->nck) ? tp->nsteps - (int64_t)c * tp->every : tp->every;
-        for (int64_t i = 0; i < len; ++i) TK(tp, one_step(H, st), "step kernel");
+        const int rc = tf_lbm_step(H, len, stream);
+        if (rc) return rc;
     }
     TK(tp, cudaMemcpyAsync(ck + tp->nck * tp->state_bytes, H->buf[H->cur], tp->state_bytes, cudaMemcpyDeviceToDevice, st),
        "final state copy");
@@ -382,21 +452,26 @@ int tf_lbm_tape_backward(tf_lbm_tape* tp, const void* grad_h, void* grad_theta, 
     const int saved_cur = H->cur;
     for (int c = tp->nck - 1; c >= 0; --c) {
         const int64_t len = (c + 1 == tp->nck) ? tp->nsteps - (int64_t)c * tp->every : tp->every;
-        // restore the checkpoint and recompute the segment's states
+        // restore the checkpoint, recompute the segment's states, then run
+        // the adjoint back through them; full segments replay captured graphs
         TK(tp, cudaMemcpyAsync(H->buf[H->cur], ck + c * tp->state_bytes, tp->state_bytes, cudaMemcpyDeviceToDevice, st),
            "checkpoint restore");
-        for (int64_t i = 0; i < len; ++i) {
-            TK(tp, aux_export_state(H->desc, H->buf[H->cur], seg + i * sbytes, H->G, st), "export kernel");
-            if (i + 1 < len) {
-                TK(tp, launch_one_step(H, H->cur, st), "step kernel");
-                H->cur ^= 1;
-            }
+        if (len == tp->every && len > 1) {
+            const int from = H->cur, afrom = cur;
+            if (!tp->g_rec[from])
+                TK(tp, capture(tp, &tp->g_rec[from], [&](cudaStream_t cs) { return recompute(tp, from, len, cs); }),
+                   "recompute graph");
+            if (!tp->g_adj[afrom])
+                TK(tp, capture(tp, &tp->g_adj[afrom], [&](cudaStream_t cs) { return adjoint_chain(tp, afrom, len, cs); }),
+                   "adjoint graph");
+            TK(tp, cudaGraphLaunch(tp->g_rec[from], st), "cudaGraphLaunch");
+            TK(tp, cudaGraphLaunch(tp->g_adj[afrom], st), "cudaGraphLaunch");
+        } else {
+            TK(tp, recompute(tp, H->cur, len, st), "recompute");
+            TK(tp, adjoint_chain(tp, cur, len, st), "adjoint chain");
         }
-        for (int64_t i = len - 1; i >= 0; --i) {
-            TK(tp, adjoint_step_dispatch(H, seg + i * sbytes, ab + cur * sbytes, ab + (cur ^ 1) * sbytes, tp->gk, st),
-               "adjoint kernels");
-            cur ^= 1;
-        }
+        H->cur ^= (int)((len - 1) & 1);
+        cur ^= (int)(len & 1);
     }
     // the handle returns to the final state of the forward
     H->cur = saved_cur;
@@ -425,6 +500,11 @@ void tf_lbm_tape_destroy(tf_lbm_tape* tp)
     cudaDeviceSynchronize();
     for (void* p : {tp->ck, tp->seg, tp->abuf, tp->gk, tp->h0, tp->theta})
         if (p) cudaFree(p);
+    for (auto& g : tp->g_rec)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& g : tp->g_adj)
+        if (g) cudaGraphExecDestroy(g);
+    if (tp->cap) cudaStreamDestroy(tp->cap);
     delete tp;
 }
 

@@ -141,6 +141,17 @@ namespace tflbm {
 void set_thread_error(const std::string& msg) { g_init_err = msg; }
 
 int handle_fail(tf_lbm_handle* H, int code, const std::string& msg) { return fail(H, code, msg); }
+int handle_check_dev_ptr(tf_lbm_handle* H, const void* ptr, const char* name, bool allow_null)
+{
+    return check_dev_ptr(H, ptr, name, allow_null);
+}
+void handle_drop_graphs(tf_lbm_handle* H) { drop_graphs(H); }
+int sm_count()
+{
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
 int handle_cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what) { return cuda_fail(H, e, what); }
 
 template <typename T>
@@ -445,6 +456,7 @@ void tf_lbm_destroy(tf_lbm_handle* H)
     if (H->flag) cudaFree(H->flag);
     if (H->diag) cudaFree(H->diag);
     if (H->adj) cudaFree(H->adj);
+    if (H->dscr) cudaFree(H->dscr);
     delete H;
 }
 

@@ -267,6 +267,124 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partial(Pops<T, SM> P, Ge
     block_store(a, partials);
 }
 
+// Thread 0 of the block receives the block's compensated sum / maximum.
+__device__ __forceinline__ Comp block_sum(Comp a)
+{
+    __shared__ Comp sm[kMassThreads / 32];
+    a = warp_reduce(a);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();  // sm may still be read from a previous call
+    if (lane == 0) sm[wid] = a;
+    __syncthreads();
+    Comp b{0.0, 0.0};
+    if (wid == 0) {
+        b = lane < kMassThreads / 32 ? sm[lane] : Comp{0.0, 0.0};
+        b = warp_reduce(b);
+    }
+    return b;
+}
+
+__device__ __forceinline__ double block_max(double v)
+{
+    __shared__ double sm[kMassThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    double b = -INFINITY;
+    if (wid == 0) {
+        b = lane < kMassThreads / 32 ? sm[lane] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    return b;
+}
+
+template <typename T, typename SM>
+__device__ __forceinline__ Pops<T, SM> pops_of(const BatchDomain<T>& D, int parity)
+{
+    Pops<T, SM> P;
+    P.f0 = (T*)D.buf[parity];
+    P.fm = (SM*)((char*)D.buf[parity] + D.G.plane * sizeof(T));
+    P.plane = D.G.plane;
+    P.pitch = D.G.pitch;
+    P.href = D.C.href;
+    P.mscale = D.C.mscale;
+    P.minv = D.C.minv;
+    P.r_axis = D.C.r_axis;
+    P.r_diag = D.C.r_diag;
+    return P;
+}
+
+// Film diagnostics of domain blockIdx.y of a table: compensated sums of h
+// over the lattice and, over the wetted nodes (h > h_wet), of h, j_x, j_y and
+// 1; and the largest h.  Block b writes kDiagPartial doubles at
+// partials[(domain * gridDim.x + b) * kDiagPartial].
+constexpr int kDiagPartial = 2 * kDiagSums + 1;
+template <typename T, typename SM>
+__global__ void __launch_bounds__(kMassThreads) k_diag_partial(const BatchDomain<T>* __restrict__ doms, int parity,
+                                                               double h_wet, double* partials)
+{
+    const BatchDomain<T>& D = doms[blockIdx.y];
+    const Pops<T, SM> P = pops_of<T, SM>(D, parity);
+    const Geom G = D.G;
+    Comp a[kDiagSums];
+#pragma unroll
+    for (int k = 0; k < kDiagSums; ++k) a[k] = Comp{0.0, 0.0};
+    double hmax = -INFINITY;
+    const long long n = (long long)G.nx * G.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T v[9], hh, jx, jy;
+        pull_at(P, G, (int)(i % G.nx), (int)(i / G.nx), v);
+        moments9(v, hh, jx, jy);
+        const double h = (double)hh;
+        comp_add(a[0], h);
+        if (h > h_wet) {
+            comp_add(a[1], h);
+            comp_add(a[2], (double)jx);
+            comp_add(a[3], (double)jy);
+            a[4].s += 1.0;  // exact below 2^53
+        }
+        hmax = fmax(hmax, h);
+    }
+    double* out = partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kDiagPartial;
+#pragma unroll
+    for (int k = 0; k < kDiagSums; ++k) {
+        const Comp b = block_sum(a[k]);
+        if (threadIdx.x == 0) {
+            out[2 * k] = b.s;
+            out[2 * k + 1] = b.c;
+        }
+    }
+    const double m = block_max(hmax);
+    if (threadIdx.x == 0) out[2 * kDiagSums] = m;
+}
+
+// One block per domain: reduce the partials of its nb blocks into
+// out[domain * kDiagOut ..]: the five sums, then the maximum.
+__global__ void __launch_bounds__(kMassThreads) k_diag_final(const double* __restrict__ partials, int nb,
+                                                             double* out)
+{
+    const double* p = partials + (long long)blockIdx.x * nb * kDiagPartial;
+    double* o = out + (long long)blockIdx.x * kDiagOut;
+    for (int k = 0; k < kDiagSums; ++k) {
+        Comp a{0.0, 0.0};
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            comp_add(a, p[i * kDiagPartial + 2 * k]);
+            a.c += p[i * kDiagPartial + 2 * k + 1];
+        }
+        const Comp b = block_sum(a);
+        if (threadIdx.x == 0) o[k] = b.s + b.c;
+    }
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, p[i * kDiagPartial + 2 * kDiagSums]);
+    m = block_max(m);
+    if (threadIdx.x == 0) o[kDiagSums] = m;
+}
+
 // Plain compensated sum of n values (used for the mean initial height).
 template <typename T>
 __global__ void __launch_bounds__(kMassThreads) k_sum_partial(const T* __restrict__ x, long long n,
@@ -401,6 +519,16 @@ cudaError_t mass_t(const StoreDesc& D, const void* f, const Geom& G, double* par
 }
 
 template <typename T, typename SM>
+cudaError_t diag_t(const void* doms, int ndom, int parity, double h_wet, double* partials, int nb, double* out,
+                   cudaStream_t st)
+{
+    k_diag_partial<T, SM><<<dim3(nb, ndom), kMassThreads, 0, st>>>((const BatchDomain<T>*)doms, parity, h_wet,
+                                                                  partials);
+    k_diag_final<<<ndom, kMassThreads, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
 cudaError_t check_t(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st)
 {
     k_check<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), G, flag);
@@ -475,6 +603,18 @@ cudaError_t aux_mass(const StoreDesc& D, const void* f, const Geom& G, double* p
                      double* result, cudaStream_t st)
 {
     TFLBM_DISPATCH(D, (mass_t<T, SM>(D, f, G, partials, nblocks, result, st)))
+}
+
+cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, double* partials, int nb,
+                     double* out, cudaStream_t st)
+{
+    switch (store) {
+        case kStoreF32: return diag_t<float, float>(doms, ndom, parity, h_wet, partials, nb, out, st);
+        case kStoreF64: return diag_t<double, double>(doms, ndom, parity, h_wet, partials, nb, out, st);
+        case kStoreF16: return diag_t<float, __half>(doms, ndom, parity, h_wet, partials, nb, out, st);
+        case kStoreBF16: return diag_t<float, __nv_bfloat16>(doms, ndom, parity, h_wet, partials, nb, out, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* flag, cudaStream_t st)

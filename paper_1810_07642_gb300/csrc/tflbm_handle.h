@@ -37,6 +37,7 @@ struct tf_lbm_handle {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::string err;
     void* adj = nullptr;       // adjoint scratch (lazy): 10 fields of the compute type
+    void* dscr = nullptr;      // diagnostics scratch (lazy): one BatchDomain entry + partial sums
 };
 
 
@@ -49,6 +50,12 @@ cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st);
 // Record an error message on H (or for the calling thread when H is null).
 int handle_fail(tf_lbm_handle* H, int code, const std::string& msg);
 int handle_cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what);
+// ARG error unless ptr is device or managed memory of the current device.
+int handle_check_dev_ptr(tf_lbm_handle* H, const void* ptr, const char* name, bool allow_null);
+// Forget the handle's captured step graphs (after a launch-shape change).
+void handle_drop_graphs(tf_lbm_handle* H);
+// Streaming multiprocessors of the current device.
+int sm_count();
 // Adjoint of one step (tflbm_adjoint.cu).
 cudaError_t adjoint_step_dispatch(tf_lbm_handle* H, const void* f, const void* a_next, void* a,
                                   void* grad_kappa, cudaStream_t st);

@@ -62,6 +62,36 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
 // Resident CTAs per SM of the step kernel for a launch shape (0 if unknown).
 int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield);
 
+// One work item of the batched step: a band of a strip of one domain.
+struct BatchItem {
+    int dom, strip, band, nbands;
+};
+// One domain of a batch, as the batched step kernel reads it.
+template <typename T>
+struct BatchDomain {
+    Geom G;
+    Consts<T> C;
+    void* buf[2];
+    const T* kappa;  // [ny][nx] or null
+};
+// One batched step: `grid` CTAs of block_x threads over `nitems` items
+// (grid == nitems without a queue).  doms points at BatchDomain<compute
+// type>[count] in device memory; queue (2 ints, zero between launches) or
+// null.  With query_occupancy set nothing is launched: the resident CTAs per
+// SM of the selected kernel are written there instead.
+struct BatchLaunch {
+    int block_x;
+    bool omega1, kfield;
+    const BatchItem* items;
+    int nitems;
+    const void* doms;
+    int parity;
+    int* queue;
+    int grid;
+    int* query_occupancy;
+};
+cudaError_t launch_step_batch(int store, const BatchLaunch& L, cudaStream_t st);
+
 // Storage convention: plane 0 holds f_0 - href, planes 1..8 hold f_l (or its
 // 16-bit encoding, see Consts).  In
 // this model the rest population carries almost all of h (f_0 ~ h, the moving
@@ -91,6 +121,14 @@ cudaError_t aux_check(const StoreDesc& D, const void* f, const Geom& G, int* fla
 cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st);
 // post-streaming populations in the compute type, [9][ny][nx]
+// Film diagnostics of each domain of a BatchDomain table (buffer `parity`):
+// out[d * kDiagOut + k] = sum h, sum of h / j_x / j_y / 1 over nodes with
+// h > h_wet, max h.  partials holds ndom * nb * (2 kDiagSums + 1) doubles.
+constexpr int kDiagSums = 5;
+constexpr int kDiagOut = kDiagSums + 1;
+inline size_t diag_partials(int ndom, int nb) { return (size_t)ndom * nb * (2 * kDiagSums + 1); }
+cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, double* partials, int nb,
+                     double* out, cudaStream_t st);
 cudaError_t aux_export_state(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
                       double hstar, cudaStream_t st);

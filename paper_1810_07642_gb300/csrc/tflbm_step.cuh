@@ -269,23 +269,23 @@ struct Band {
 };
 
 template <int BX>
-__device__ __forceinline__ Band make_band(const Geom& G, int t)
+__device__ __forceinline__ Band make_band(const Geom& G, int t, int strip, int band, int nbands)
 {
     Band b;
     constexpr int W = BX - 4;
-    b.x0 = blockIdx.x * W;                      // first output column
+    b.x0 = strip * W;                           // first output column
     b.weff = min(W, G.nx - b.x0);               // output columns of this CTA
     b.hcol = t < b.weff + 4;                    // forms h
     b.pcol = t >= 1 && t < b.weff + 3;          // forms p
     b.ocol = t >= 2 && t < b.weff + 2;          // collides and stores
-    b.ybeg = (int)(((long long)blockIdx.y * G.ny) / gridDim.y);
-    b.yend = (int)(((long long)(blockIdx.y + 1) * G.ny) / gridDim.y);
+    b.ybeg = (int)(((long long)band * G.ny) / nbands);
+    b.yend = (int)(((long long)(band + 1) * G.ny) / nbands);
     // March direction: even bands go +y, odd bands -y, so two neighbouring
     // bands read the rows around their common edge at the same time (both at
     // the start or both at the end of the kernel) and the second read hits
     // L2.  March step k forms h of row r(k) = rstart + k dir, the pressure of
     // row r(k-1) and collides row r(k-3), for k = 0 .. R+4.
-    b.dir = (blockIdx.y & 1) ? -1 : 1;
+    b.dir = (band & 1) ? -1 : 1;
     b.R = b.yend - b.ybeg;
     b.rstart = b.dir > 0 ? b.ybeg - 2 : b.yend + 1;
     return b;
@@ -295,15 +295,16 @@ __device__ __forceinline__ Band make_band(const Geom& G, int t)
 // Kernel 1: every thread loads its own nine pulled populations from global
 // memory, one row ahead of use (register prefetch).
 template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
-k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
-       SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
+__device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* __restrict__ finm,
+                                          T* __restrict__ fout0, SM* __restrict__ foutm,
+                                          const T* __restrict__ kappa, const Geom& G, const Consts<T>& C,
+                                          int strip, int band, int nbands)
 {
     __shared__ T hsm[4][BX];  // h - href ring: slot t = column x0 - 2 + t
     __shared__ T psm[4][BX];  // p ring, same columns
     const int t = threadIdx.x;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
-    const Band B = make_band<BX>(G, t);
+    const Band B = make_band<BX>(G, t, strip, band, nbands);
     const bool disj = KFIELD || C.kappa_u != T(0);
     const int dir = B.dir, R = B.R;
 
@@ -379,6 +380,66 @@ k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ 
         if (++k > last) break;
         body(std::integral_constant<int, 3>{}, k);
         if (++k > last) break;
+    }
+}
+
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
+k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
+       SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
+{
+    step_band<SM, T, BX, OMEGA1, KFIELD>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
+                                         gridDim.y);
+}
+
+// One batched step.  Each work item is one band of one strip of one domain;
+// every domain reads its buffer `parity` and writes the other one.  Domains
+// share the storage type, the omega == 1 property and the presence of a kappa
+// field (a uniform kappa is passed as a filled field).  With queue == null,
+// CTA i takes item i (the hardware block scheduler is the work queue); else
+// the grid is persistent and each CTA takes items from the counter queue[0]
+// until they run out, and the last CTA to finish resets queue[0..1] to zero
+// for the next launch.  No CTA ever waits on another.
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+__device__ __forceinline__ void batch_item(const BatchItem it, const BatchDomain<T>* __restrict__ doms,
+                                           int parity)
+{
+    const BatchDomain<T>& D = doms[it.dom];
+    const Geom G = D.G;
+    const Consts<T> C = D.C;
+    const void* fin = D.buf[parity];
+    void* fout = D.buf[parity ^ 1];
+    const T* f0 = (const T*)fin;
+    const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(T));
+    T* g0 = (T*)fout;
+    SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
+    step_band<SM, T, BX, OMEGA1, KFIELD>(f0, fm, g0, gm, D.kappa, G, C, it.strip, it.band, it.nbands);
+}
+
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
+k_step_batch(const BatchItem* __restrict__ items, int nitems, const BatchDomain<T>* __restrict__ doms,
+             int parity, int* queue)
+{
+    if (!queue) {
+        batch_item<SM, T, BX, OMEGA1, KFIELD>(items[blockIdx.x], doms, parity);
+        return;
+    }
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();  // the previous item is done with the shared rings and with `next`
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int i = next;
+        if (i >= nitems) break;
+        batch_item<SM, T, BX, OMEGA1, KFIELD>(items[i], doms, parity);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {  // every CTA has taken its last item
+            queue[0] = 0;
+            queue[1] = 0;
+        }
     }
 }
 
@@ -503,7 +564,7 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
 
     const int t = threadIdx.x;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
-    const Band B = make_band<BX>(G, t);
+    const Band B = make_band<BX>(G, t, blockIdx.x, blockIdx.y, gridDim.y);
     const bool disj = KFIELD || C.kappa_u != T(0);
     const int dir = B.dir, R = B.R;
     const int x = wrap_index(B.x0 - 2 + t, nx);
@@ -665,6 +726,38 @@ cudaError_t launch_step_bx(int pipeline, const T* fin0, const SM* finm, T* fout0
     }
     if (om1) return launch_one<SM, T, BX, true, false>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
     return launch_one<SM, T, BX, false, false>(pipeline, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+}
+
+template <typename SM, typename T, int BX, bool OM1, bool KF>
+cudaError_t batch_one(const BatchLaunch& L, cudaStream_t st)
+{
+    const BatchDomain<T>* d = (const BatchDomain<T>*)L.doms;
+    if (L.query_occupancy) {
+        int n = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batch<SM, T, BX, OM1, KF>, BX, 0);
+        *L.query_occupancy = e == cudaSuccess ? n : 0;
+        return e;
+    }
+    k_step_batch<SM, T, BX, OM1, KF><<<L.grid, BX, 0, st>>>(L.items, L.nitems, d, L.parity, L.queue);
+    return cudaGetLastError();
+}
+
+template <typename SM, typename T, int BX>
+cudaError_t batch_bx(const BatchLaunch& L, cudaStream_t st)
+{
+    if (L.kfield) return L.omega1 ? batch_one<SM, T, BX, true, true>(L, st) : batch_one<SM, T, BX, false, true>(L, st);
+    return L.omega1 ? batch_one<SM, T, BX, true, false>(L, st) : batch_one<SM, T, BX, false, false>(L, st);
+}
+
+template <typename SM, typename T>
+cudaError_t launch_batch_typed(const BatchLaunch& L, cudaStream_t st)
+{
+    switch (L.block_x) {
+        case 64: return batch_bx<SM, T, 64>(L, st);
+        case 128: return batch_bx<SM, T, 128>(L, st);
+        case 256: return batch_bx<SM, T, 256>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Resident CTAs per SM of one instantiation (for sizing the grid).

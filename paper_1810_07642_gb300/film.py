@@ -119,10 +119,85 @@ class ThinFilm:
                             cur["graph_chunk"] if graph_chunk is None else graph_chunk,
                             cur["pipeline"] if pipeline is None else pipeline)
 
+    def tune(self, trial_steps: int = 16):
+        """Time candidate launch shapes on this run's own state, keep the
+        fastest and return it (the state and time are left as they were)."""
+        l = L.tf_lbm_tune(self.handle, trial_steps, self._st)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, pipeline=l.pipeline)
+
+    def diagnostics(self, h_wet: float, out=None):
+        """Film diagnostics of the current state (a float64 tensor of the six
+        tf_lbm_diag fields, on the device; no host synchronisation)."""
+        if out is None:
+            out = torch.empty(len(L.DIAG_FIELDS), dtype=torch.float64, device=self.device)
+        L.tf_lbm_diagnostics(self.handle, h_wet, out.data_ptr(), self._st)
+        return out
+
     def close(self):
         if getattr(self, "handle", None):
             L.tf_lbm_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class FilmBatch:
+    """Many independent ThinFilm runs of uneven sizes (one dtype) advanced by
+    one batched launch per step (tf_lbm_batch_*).  The films stay usable on
+    their own (state, moments, mass) and must outlive the batch."""
+
+    def __init__(self, films, stream=None):
+        self.films = list(films)
+        if not self.films:
+            raise ValueError("a batch needs at least one film")
+        self._st = _stream_ptr(stream)
+        self.device = self.films[0].device
+        self.batch = L.tf_lbm_batch_create([f.handle for f in self.films], self._st)
+
+    def step(self, nsteps: int = 1):
+        L.tf_lbm_batch_step(self.batch, nsteps, self._st)
+
+    @property
+    def items(self) -> int:
+        return L.tf_lbm_batch_items(self.batch)
+
+    @property
+    def launch(self):
+        l = L.tf_lbm_batch_get_launch(self.batch)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue)
+
+    def set_launch(self, block_x=None, rows=None, graph_chunk=None, queue=None):
+        cur = self.launch
+        L.tf_lbm_batch_set_launch(self.batch, block_x or cur["block_x"], rows or cur["rows"],
+                                  cur["graph_chunk"] if graph_chunk is None else graph_chunk,
+                                  cur["queue"] if queue is None else queue)
+
+    def tune(self, trial_steps: int = 16):
+        l = L.tf_lbm_batch_tune(self.batch, trial_steps, self._st)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue)
+
+    def diagnostics(self, h_wet: float, out=None):
+        """(count, 6) float64 device tensor of tf_lbm_diag rows, one per film."""
+        if out is None:
+            out = torch.empty((len(self.films), len(L.DIAG_FIELDS)), dtype=torch.float64,
+                              device=self.device)
+        L.tf_lbm_batch_diagnostics(self.batch, h_wet, out.data_ptr(), self._st)
+        return out
+
+    def close(self):
+        if getattr(self, "batch", None):
+            L.tf_lbm_batch_destroy(self.batch)
+            self.batch = None
 
     def __del__(self):
         try:
