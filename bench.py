@@ -250,6 +250,94 @@ def adjoint_cost(n: int = 512, nsteps: int = 20000):
             "backward_over_forward": (t_grad - t_tape) / t_fwd}
 
 
+def batched_sweep(steps: int = 30000, timed: int = 400):
+    """The batched sliding-drop sweep: 64 uneven domains (256x128 .. 1024x512,
+    FP32, uniform theta = 40 deg, delta = 1, tangential body force from Bond
+    numbers log-spaced over 0.05 .. 1).  MLUPS of one batched launch per step
+    (default and autotuned shape) against the same domains stepped one after
+    another by single-domain launches; the batched path's error against the
+    FP64 oracle on four reduced domains; and the steady capillary number
+    Ca = nu U / gamma against Bo after `steps` steps, U the wetted-region
+    momentum over the wetted mass (h > 2 h*), reduced on the device."""
+    import torch
+    import oracle as O
+    from paper_1810_07642_gb300 import inputs
+    from paper_1810_07642_gb300.film import FilmBatch, ThinFilm
+
+    def films_of(specs):
+        return [ThinFilm(dict(p, theta_uniform=float(th[0, 0])), h0, None) for h0, th, p in specs]
+
+    def mlups(fn, nodes, k):
+        fn(4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn(k)
+        e1.record()
+        torch.cuda.synchronize()
+        return nodes * k / e0.elapsed_time(e1) / 1e3
+
+    specs = inputs.sliding_drops(count=64, seed=0)
+    films = films_of(specs)
+    nodes = sum(f.nx * f.ny for f in films)
+
+    def seq(k):
+        for f in films:
+            f.step(k)
+
+    out = {"domains": len(films), "nodes": nodes}
+    out["mlups_single_domain_launches"] = mlups(seq, nodes, timed)
+    B = FilmBatch(films)
+    out["default_launch"] = B.launch
+    out["mlups_batched_default"] = mlups(B.step, nodes, timed)
+    out["tuned_launch"] = B.tune(16)
+    out["items"] = B.items
+    out["mlups_batched_tuned"] = mlups(B.step, nodes, timed)
+    out["speedup_batched_over_single_domain_launches"] = (out["mlups_batched_tuned"] /
+                                                         out["mlups_single_domain_launches"])
+    B.close()
+    for f in films:
+        f.close()
+    # Ca vs Bo (the paper's sliding-drop study), fresh runs in the tuned shape
+    films = films_of(specs)
+    B = FilmBatch(films)
+    B.set_launch(**out["tuned_launch"])
+    h_wet = 2 * inputs.DEFAULTS["hstar"]
+    B.step(steps)
+    d = B.diagnostics(h_wet).cpu().numpy()
+    nu = (specs[0][2]["tau"] - 0.5) / 3.0
+    gamma = specs[0][2]["gamma"]
+    bo = np.array([p["bond"] for _, _, p in specs])
+    ca = nu * (d[:, 2] / d[:, 1]) / gamma
+    sl = bo >= 0.2
+    slope, icpt = np.polyfit(bo[sl], ca[sl], 1)
+    fit = slope * bo[sl] + icpt
+    r2 = 1 - ((ca[sl] - fit) ** 2).sum() / ((ca[sl] - ca[sl].mean()) ** 2).sum()
+    out["ca_vs_bo"] = {"steps": steps, "bo": [round(float(x), 4) for x in bo],
+                       "ca": [float(f"{x:.4g}") for x in ca],
+                       "fit_bo_ge_0.2": {"slope": float(slope), "bo_c": float(-icpt / slope),
+                                         "r2": float(r2)},
+                       "check_status_nonzero": int(sum(1 for f in films if f.check()))}
+    B.close()
+    for f in films:
+        f.close()
+    # accuracy of the batched path: four reduced sweep domains, 1000 steps
+    small = inputs.sliding_drops(count=4, seed=1, lx_range=(128, 256))
+    sf = films_of(small)
+    err = 0.0
+    with FilmBatch(sf) as SB:
+        SB.step(1000)
+        for f, (h0, th, p) in zip(sf, small):
+            cfg = O.Config(**{k: v for k, v in p.items() if k in O.Config.__dataclass_fields__})
+            _, ho, _, _ = O.run(cfg, h0, th, 1000)
+            h = f.h().double().cpu().numpy()
+            err = max(err, float(np.abs(h - ho).max() / np.abs(ho).max()))
+    for f in sf:
+        f.close()
+    out["rel_linf_h_vs_oracle_4_domains_1000"] = err
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
     2048 x R periodic band of the workload, R sized to fit a few minutes."""
@@ -389,6 +477,7 @@ def run_tflbm(args):
     if world == 1 and not args.skip_extras:
         extras["storage"] = storage_variants()
         extras["adjoint"] = adjoint_cost()
+        extras["batched_sweep"] = batched_sweep()
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -419,19 +508,97 @@ def run_tflbm(args):
     return 0
 
 
+def run_sweep(args):
+    """--workload sweep: the batched sliding-drop sweep as the timed step (one
+    batched launch per step over all 64 domains, autotuned shape)."""
+    import torch
+    from paper_1810_07642_gb300 import build, inputs
+    from paper_1810_07642_gb300.film import FilmBatch, ThinFilm
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    specs = inputs.sliding_drops(count=64, seed=rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        films = [ThinFilm(dict(p, theta_uniform=float(th[0, 0])), h0, None, stream=stream)
+                 for h0, th, p in specs]
+        B = FilmBatch(films, stream=stream)
+    nodes = sum(f.nx * f.ny for f in films)
+    if args.batch_launch:
+        bx, rows, chunk, queue = (int(v) for v in args.batch_launch.split(","))
+        B.set_launch(block_x=bx, rows=rows, graph_chunk=chunk, queue=queue)
+        launch = B.launch
+    else:
+        launch = B.tune(16)
+    B.step(args.warmup)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        B.step(args.steps)
+        ev1.record(stream)
+        stream.synchronize()
+    if dist:
+        dist.barrier()
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    t_max = max_over_ranks(t_local, dist, "cuda")
+    value = aggregate_mlups(nodes, args.steps, world, t_max)
+    bpl = 72  # FP32, uniform theta: 9 populations read + 9 written
+    achieved = bpl * nodes / (t_local / args.steps) / 1e9
+    peak, peak_kind = measured_peaks()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "batched sliding-drop sweep: 64 periodic domains 256x128.."
+                                       "1024x512 (seeded), FP32, theta=40 deg, delta=1, Bo "
+                                       "log-spaced 0.05..1", "nodes": nodes, "launch": launch,
+                           "items": B.items,
+                           "l2": "inputs larger than L2 (2.3 GB populations): no flush"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_kind": f"{peak_kind} copy bandwidth",
+                             "kernel": "k_step_batch<float,float,...>"},
+                "gpu_launches": args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    B.close()
+    for f in films:
+        f.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="tflbm", choices=["tflbm", "reference"])
+    ap.add_argument("--workload", default="patterned", choices=["patterned", "sweep"],
+                    help="patterned: the 2048^2 dewetting run (default); sweep: the batched "
+                         "64-domain sliding-drop sweep as the timed step")
+    ap.add_argument("--batch-launch", default="",
+                    help="sweep workload: block_x,rows,graph_chunk,queue instead of autotuning")
     ap.add_argument("--skip-extras", action="store_true",
-                    help="skip the 16-bit storage and adjoint measurements")
+                    help="skip the 16-bit storage, adjoint and batched-sweep measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_tflbm(args)
 
 
