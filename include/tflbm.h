@@ -59,7 +59,7 @@ enum {
     TF_LBM_BF16 = 3  /* as TF_LBM_F16 with BF16 moving populations           */
 };
 /* 16-bit storage (TF_LBM_F16, TF_LBM_BF16).  The rest population carries
- * almost all of h; it is kept in FP32 as f_0 - href (href = mean of h0).  The
+ * almost all of h; it is kept in FP32 as f_0 - href (href = smallest h0).  The
  * eight moving populations are kept as deviations from the rest equilibrium
  * at href, f_l - f_eq_l(href, 0), in FP16 scaled by 2^10 or in BF16.  Every
  * value is decoded to FP32 before use, and the 16-bit rounding of each

@@ -279,3 +279,69 @@ def run(cfg: Config, h0: np.ndarray, theta, nsteps: int):
     step(cfg, kap, f, nsteps)
     h, ux, uy = moments(cfg, f)
     return f, h, ux, uy
+
+
+# ---------------------------------------------------------------- diagnostics
+# Plain definitions of the film diagnostics of Section III and the appendix,
+# evaluated on a post-streaming state f (test infrastructure, like the rest).
+
+DIAG_FIELDS = ("mass", "wet_mass", "wet_jx", "wet_jy", "wet_area", "h_max",
+               "wet_cos_x", "wet_sin_x", "wet_cos_y", "wet_sin_y", "mode_cos", "mode_sin")
+
+
+def film_diagnostics(cfg: Config, f: np.ndarray, h_wet: float, mode=(1, 0)) -> np.ndarray:
+    """Film diagnostics of the state f, in the order of DIAG_FIELDS:
+    sum of h over the lattice; over the wetted nodes W = {h > h_wet} the sums
+    of h, of j = sum_l c_l f_l (two components) and of 1; the largest h; the
+    circular first moments of the wetted film, sum_W h cos(2 pi x / nx),
+    sum_W h sin(2 pi x / nx) and the same in y (the drop's position on the
+    periodic lattice is their angle); and the Fourier sums of h over the
+    whole lattice at the wave vector 2 pi (mx / nx, my / ny) (a single-mode
+    amplitude, Sec. III A, is 2 |sum| / (nx ny)).  Section II gives h and j
+    as the zeroth and first moments."""
+    c = lattice()[0]
+    h = f.sum(axis=0)
+    jx = np.tensordot(c[:, 0], f, axes=1)
+    jy = np.tensordot(c[:, 1], f, axes=1)
+    w = h > h_wet
+    ny, nx = h.shape
+    ax = 2 * np.pi * np.arange(nx) / nx
+    ay = 2 * np.pi * np.arange(ny) / ny
+    hw = np.where(w, h, 0.0)
+    mx, my = mode
+    ph = 2 * np.pi * (mx * np.arange(nx)[None, :] / nx + my * np.arange(ny)[:, None] / ny)
+    return np.array([
+        h.sum(), hw.sum(), jx[w].sum(), jy[w].sum(), float(w.sum()), h.max(),
+        (hw * np.cos(ax)[None, :]).sum(), (hw * np.sin(ax)[None, :]).sum(),
+        (hw * np.cos(ay)[:, None]).sum(), (hw * np.sin(ay)[:, None]).sum(),
+        (h * np.cos(ph)).sum(), (h * np.sin(ph)).sum()])
+
+
+def term_norms(cfg: Config, kap: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """L2 norms, ||phi||_2 = (sum phi^2 / (nx ny))^(1/2) (appendix, Eq.
+    magnitude), of the x-components of the three momentum terms the appendix
+    compares: the film-pressure term -h d_x p, the friction -nu alpha(h) u_x
+    (Eqs. forcefric, alphafric) and the longitudinal dissipation
+    nu lap(h u_x) + 2 nu d_x(div(h u)).  p is the film pressure of Eq.
+    (pfilm); d_x and div use the gradient stencil of Eq. (derivative) and lap
+    the Laplacian of Eq. (n_laplace), each a pinned oracle routine."""
+    h, ux, uy = moments(cfg, f)
+    p, _, _ = pressure_force(cfg, kap, f)
+    nu = (cfg.tau - 0.5) / 3.0
+    a = np.vectorize(lambda hh: alpha(hh, cfg.delta))(h)
+    jx, jy = h * ux, h * uy
+    div = gradient(jx)[0] + gradient(jy)[1]
+    terms = (-h * gradient(p)[0], -nu * a * ux, nu * laplacian(jx) + 2 * nu * gradient(div)[0])
+    return np.array([np.sqrt((t ** 2).mean()) for t in terms])
+
+
+def drop_geometry(wet_area: float, h_apex: float, hstar: float):
+    """Contact radius, cap radius and contact angle of a spherical-cap drop
+    (Sec. III B): r = sqrt(A / pi) from the wetted area, apex height
+    h_d = h_max - h_*, R = (r^2 + h_d^2) / (2 h_d) and theta = arcsin(r / R)
+    (pi - arcsin when h_d > r)."""
+    r = np.sqrt(wet_area / np.pi)
+    hd = h_apex - hstar
+    R = (r * r + hd * hd) / (2 * hd)
+    th = np.arcsin(np.clip(r / R, -1.0, 1.0))
+    return r, R, (np.pi - th) if hd > r else th

@@ -173,6 +173,8 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.minv = T(H->desc.minv);
     C.r_axis = T(H->desc.r_axis);
     C.r_diag = T(H->desc.r_diag);
+    C.nr_axis = T(-H->desc.r_axis * H->desc.mscale);
+    C.nr_diag = T(-H->desc.r_diag * H->desc.mscale);
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
     C.status = H->status;
@@ -265,15 +267,18 @@ int tf_lbm_init(tf_lbm_handle** out, const tf_lbm_params* params, const void* h0
     } else {
         H->kappa_u = (1.0 - cos(params->theta_uniform)) * kscale;
     }
-    // reference height: the mean of h0, rounded to the storage type
-    e = aux_sum(H->dbl, h0, n, H->partials, H->nmass, H->result, st);
-    if (e != cudaSuccess) return bail(cuda_fail(H, e, "sum kernel"));
-    double hsum = 0.0;
-    if ((e = cudaMemcpyAsync(&hsum, H->result, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+    // Reference height: the smallest h0, rounded to the storage type.  Plane
+    // 0 stores f_0 - href, so FP32 resolves h - href to 2^-24 of |h - href|:
+    // the thin parts of a film (precursor, contact lines), where the
+    // disjoining pressure is stiffest and rounding differences grow fastest,
+    // get the finest resolution, while thick parts keep 2^-24 relative.
+    e = aux_min(H->dbl, h0, n, H->partials, H->nmass, H->result, st);
+    if (e != cudaSuccess) return bail(cuda_fail(H, e, "min kernel"));
+    double hmin = 0.0;
+    if ((e = cudaMemcpyAsync(&hmin, H->result, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return bail(cuda_fail(H, e, "reading the mean height"));
-    const double mean = hsum / (double)n;
-    H->href = H->dbl ? mean : (double)(float)mean;
+        return bail(cuda_fail(H, e, "reading the smallest height"));
+    H->href = H->dbl ? hmin : (double)(float)hmin;
     if (!isfinite(H->href)) H->href = 0.0;  // a non-finite h0 is reported by tf_lbm_check
     // 16-bit storage of the moving populations: deviations from the rest
     // equilibrium at href, scaled by 2^10 in FP16 (keeps small deviations out

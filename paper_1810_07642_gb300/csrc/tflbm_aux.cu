@@ -385,16 +385,25 @@ __global__ void __launch_bounds__(kMassThreads) k_diag_final(const double* __res
     if (threadIdx.x == 0) o[kDiagSums] = m;
 }
 
-// Plain compensated sum of n values (used for the mean initial height).
+// Smallest of n values (NaNs ignored; +inf when there is none).
 template <typename T>
-__global__ void __launch_bounds__(kMassThreads) k_sum_partial(const T* __restrict__ x, long long n,
+__global__ void __launch_bounds__(kMassThreads) k_min_partial(const T* __restrict__ x, long long n,
                                                               double* partials)
 {
-    Comp a{0.0, 0.0};
+    double m = -INFINITY;  // max of -x
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        comp_add(a, (double)x[i]);
-    block_store(a, partials);
+        m = fmax(m, -(double)x[i]);
+    m = block_max(m);
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
+
+__global__ void __launch_bounds__(kMassThreads) k_min_final(const double* partials, int n, double* out)
+{
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, partials[i]);
+    m = block_max(m);
+    if (threadIdx.x == 0) *out = -m;
 }
 
 __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* partials, int n, double* out)
@@ -647,13 +656,14 @@ cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, 
     return cudaGetLastError();
 }
 
-cudaError_t aux_sum(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
+cudaError_t aux_min(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
                     cudaStream_t st)
 {
-    if (dbl) k_sum_partial<double><<<nblocks, kMassThreads, 0, st>>>((const double*)x, n, partials);
-    else k_sum_partial<float><<<nblocks, kMassThreads, 0, st>>>((const float*)x, n, partials);
-    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);
+    if (dbl) k_min_partial<double><<<nblocks, kMassThreads, 0, st>>>((const double*)x, n, partials);
+    else k_min_partial<float><<<nblocks, kMassThreads, 0, st>>>((const float*)x, n, partials);
+    k_min_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, result);
     return cudaGetLastError();
 }
+
 
 }  // namespace tflbm

@@ -38,6 +38,7 @@ struct Consts {
     // 16-bit storage of the moving populations: q = (f_l - R_l) * mscale,
     // R_l = f_eq_l(href, 0) = r_axis (odd l) or r_diag (even l); minv = 1/mscale
     T mscale, minv, r_axis, r_diag;
+    T nr_axis, nr_diag;  // -r_axis * mscale, -r_diag * mscale (exact: mscale is a power of 2)
     int n_exp, m_exp;
     int* status;  // device word for kStatusTimeout (may be null)
 };
@@ -132,8 +133,10 @@ cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h
 cudaError_t aux_export_state(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
                       double hstar, cudaStream_t st);
-cudaError_t aux_sum(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
+// smallest of n values of the compute type into *result (double)
+cudaError_t aux_min(bool dbl, const void* x, long long n, double* partials, int nblocks, double* result,
                     cudaStream_t st);
+
 
 // Number of partial sums the mass reduction writes (its grid size), and the
 // number the plain field sum writes.

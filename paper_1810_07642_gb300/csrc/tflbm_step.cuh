@@ -217,29 +217,53 @@ __device__ __forceinline__ void collide_store(const T* pn, const T* pc, const T*
         o8 = m * f[8] + w * (Sb - Db) - Qb;
     }
     // In 16-bit storage, round the moving populations to what the readers
-    // will reconstruct before the rest population is formed.
+    // will reconstruct before the rest population is formed (f_1 possibly
+    // after it, see below).
     SM q1, q2, q3, q4, q5, q6, q7, q8;
+    // (o - R) * mscale in one rounding: o * mscale - R * mscale is exact
+    auto narrow = [&](T& o, SM& q, T R, T NR) {
+        q = from_f<SM>(fmaf(o, C.mscale, NR));
+        o = fmaf(to_f(q), C.minv, R);
+    };
+    bool f1_last = false;
     if constexpr (NARROW) {
-        auto narrow = [&](T& o, SM& q, T R) {
-            q = from_f<SM>((o - R) * C.mscale);
-            o = fmaf(to_f(q), C.minv, R);
-        };
-        narrow(o1, q1, C.r_axis); narrow(o3, q3, C.r_axis);
-        narrow(o5, q5, C.r_axis); narrow(o7, q7, C.r_axis);
-        narrow(o2, q2, C.r_diag); narrow(o4, q4, C.r_diag);
-        narrow(o6, q6, C.r_diag); narrow(o8, q8, C.r_diag);
+        narrow(o3, q3, C.r_axis, C.nr_axis);
+        narrow(o5, q5, C.r_axis, C.nr_axis); narrow(o7, q7, C.r_axis, C.nr_axis);
+        narrow(o2, q2, C.r_diag, C.nr_diag); narrow(o4, q4, C.r_diag, C.nr_diag);
+        narrow(o6, q6, C.r_diag, C.nr_diag); narrow(o8, q8, C.r_diag, C.nr_diag);
     }
     // stored rest population: f*_0 - href = (h - href) - sum_{l>0} f*_l.  The
     // error-free sums give the exact rounding residuals of the pull sum and
     // of this subtraction.  With full-width storage they go to the opposite
     // pair (1, 5), half each, so the stored populations sum to the pulled
     // ones (mass conserved to roundings of small values) and the momentum is
-    // untouched; with 16-bit storage they are added to the rest population.
-    const T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
+    // untouched.  With 16-bit storage they are added to the rest population,
+    // and the residual of that addition is left to the finer of two
+    // roundings: the 16-bit one of f_1 - R (half-ulp 2^-11 relative in FP16,
+    // 2^-8 in BF16) or the FP32 one of f_0 - href (2^-24 relative).  Where
+    // f_1 rounds finer (a thick film that barely moves, e.g. a resting drop)
+    // the residual goes into f_1 before f_1 is rounded; elsewhere f_1 is
+    // rounded first and its own residual becomes part of the rest population.
+    T osum = ((o1 + o5) + (o3 + o7)) + ((o2 + o6) + (o4 + o8));
+    if constexpr (NARROW) {
+        constexpr float kRatio = std::is_same<SM, __half>::value ? 8192.0f : 65536.0f;
+        f1_last = fabsf(o1 - C.r_axis) * kRatio < fabsf(dh - osum);
+        if (!f1_last) {
+            const T o1u = o1;
+            narrow(o1, q1, C.r_axis, C.nr_axis);
+            osum += o1 - o1u;
+        }
+    }
     T o0v, e2;
     two_sum(dh, -osum, o0v, e2);
     if constexpr (NARROW) {
-        o0v += er + e2;
+        T o0n, e3;
+        two_sum(o0v, er + e2, o0n, e3);
+        o0v = o0n;
+        if (f1_last) {
+            o1 += e3;
+            narrow(o1, q1, C.r_axis, C.nr_axis);
+        }
     } else {
         const T half_r = (er + e2) * T(0.5);
         o1 += half_r;
