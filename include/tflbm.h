@@ -219,10 +219,16 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
 
 /* -------------------------------------------------------- diagnostics
  * Film diagnostics of the current state, computed on the device (Section
- * III: the drop's contact radius from its wetted area, its apex height, its
- * sliding velocity U from momentum over the wetted nodes, Ca = nu U / gamma
- * with rho = 1).  The wetted nodes are those with h > h_wet.  Every sum is
- * taken in double precision with compensated summation. */
+ * III): the drop's contact radius from its wetted area and its apex height
+ * (Sec. III B: r = sqrt(A / pi), R = (r^2 + h_d^2) / (2 h_d), theta =
+ * arcsin(r / R)), its position on the periodic lattice from circular first
+ * moments, its sliding velocity U from the momentum over the wetted nodes
+ * (Sec. III C: Ca = nu U / gamma with rho = 1), and the amplitude of one
+ * Fourier mode of h (Sec. III A: a single-mode amplitude is
+ * 2 |mode_cos + i mode_sin| / (nx ny)).  The wetted nodes are those with
+ * h > h_wet.  h and j are the moments of the post-streaming populations
+ * (Section II); every sum is taken in double precision with compensated
+ * summation. */
 typedef struct tf_lbm_diag {
     double mass;      /* sum of h over the lattice                          */
     double wet_mass;  /* sum of h over the wetted nodes                     */
@@ -230,11 +236,30 @@ typedef struct tf_lbm_diag {
     double wet_jy;    /* sum of j_y over the wetted nodes                   */
     double wet_area;  /* number of wetted nodes                             */
     double h_max;     /* largest h                                          */
+    double wet_cos_x; /* sum over wetted nodes of h cos(2 pi x / nx)        */
+    double wet_sin_x; /* ... h sin(2 pi x / nx)                             */
+    double wet_cos_y; /* ... h cos(2 pi y / ny)                             */
+    double wet_sin_y; /* ... h sin(2 pi y / ny)                             */
+    double mode_cos;  /* sum over the lattice of h cos(2 pi (mx x / nx + my y / ny)) */
+    double mode_sin;  /* ... h sin(...)                                     */
 } tf_lbm_diag;
-/* out: device pointer to one tf_lbm_diag (six doubles), written
- * asynchronously on `stream` (no host synchronisation).  Uses a small
- * handle-owned scratch allocated on first use. */
-int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, void* out, void* stream);
+/* out: device pointer to one tf_lbm_diag (twelve doubles), written
+ * asynchronously on `stream` (no host synchronisation).  (mode_x, mode_y)
+ * are the integer wave numbers (mx, my) of the Fourier sums.  Uses a small
+ * handle-owned scratch allocated on first use.  ARG error on a NULL or host
+ * `out` or a NaN h_wet. */
+int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, int32_t mode_x, int32_t mode_y, void* out,
+                       void* stream);
+
+/* Term balance of the paper's appendix: the L2 norms (Eq. magnitude,
+ * ||phi||_2 = (sum_x phi^2 / (nx ny))^(1/2)) of the x-components of the
+ * film-pressure term -h d_x p, the friction term -nu alpha(h) u_x (Eqs.
+ * forcefric, alphafric) and the longitudinal dissipation
+ * nu lap(h u_x) + 2 nu d_x(div(h u)), the derivatives taken with the
+ * stencils of Eqs. (derivative) and (n_laplace).  out: device pointer to
+ * three doubles in that order, written asynchronously.  Uses 5 fields of
+ * handle-owned scratch (allocated on first use). */
+int tf_lbm_term_norms(tf_lbm_handle* H, void* out, void* stream);
 
 /* --------------------------------------------------------------- batches
  * Many independent simulations of uneven sizes (a parameter sweep) advanced
@@ -277,7 +302,8 @@ int tf_lbm_batch_set_launch(tf_lbm_batch* B, const tf_lbm_batch_launch* in);
 int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch* best, void* stream);
 /* tf_lbm_diagnostics of every handle in two launches: out is a device array
  * of `count` tf_lbm_diag, in the order of the handles. */
-int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, void* out, void* stream);
+int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, int32_t mode_x, int32_t mode_y, void* out,
+                             void* stream);
 /* Number of work items of one batched step (= CTAs without the queue). */
 int32_t tf_lbm_batch_items(const tf_lbm_batch* B);
 /* Waits for the batch's device work and frees what it owns (not the

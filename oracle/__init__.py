@@ -299,10 +299,10 @@ def film_diagnostics(cfg: Config, f: np.ndarray, h_wet: float, mode=(1, 0)) -> n
     whole lattice at the wave vector 2 pi (mx / nx, my / ny) (a single-mode
     amplitude, Sec. III A, is 2 |sum| / (nx ny)).  Section II gives h and j
     as the zeroth and first moments."""
-    c = lattice()[0]
+    cx, cy, _ = lattice()
     h = f.sum(axis=0)
-    jx = np.tensordot(c[:, 0], f, axes=1)
-    jy = np.tensordot(c[:, 1], f, axes=1)
+    jx = np.tensordot(cx.astype(np.float64), f, axes=1)
+    jy = np.tensordot(cy.astype(np.float64), f, axes=1)
     w = h > h_wet
     ny, nx = h.shape
     ax = 2 * np.pi * np.arange(nx) / nx

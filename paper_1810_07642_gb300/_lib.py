@@ -25,10 +25,11 @@ EXPORTED = [
     "tf_lbm_tape_backward", "tf_lbm_tape_destroy", "tf_lbm_tune", "tf_lbm_diagnostics",
     "tf_lbm_batch_create", "tf_lbm_batch_step", "tf_lbm_batch_get_launch", "tf_lbm_batch_set_launch",
     "tf_lbm_batch_tune", "tf_lbm_batch_diagnostics", "tf_lbm_batch_items", "tf_lbm_batch_destroy",
-    "tf_lbm_batch_last_error",
+    "tf_lbm_batch_last_error", "tf_lbm_term_norms",
 ]
 # fields of tf_lbm_diag, in order
-DIAG_FIELDS = ("mass", "wet_mass", "wet_jx", "wet_jy", "wet_area", "h_max")
+DIAG_FIELDS = ("mass", "wet_mass", "wet_jx", "wet_jy", "wet_area", "h_max",
+               "wet_cos_x", "wet_sin_x", "wet_cos_y", "wet_sin_y", "mode_cos", "mode_sin")
 TF_LBM_NOALLOC_MAX_ELEMS = 67108864
 
 
@@ -105,13 +106,14 @@ def lib():
     L.tf_lbm_tape_destroy.argtypes = [_VP]
     L.tf_lbm_tape_destroy.restype = None
     L.tf_lbm_tune.argtypes = [_VP, i32, ctypes.POINTER(Launch), _VP]
-    L.tf_lbm_diagnostics.argtypes = [_VP, ctypes.c_double, _VP, _VP]
+    L.tf_lbm_diagnostics.argtypes = [_VP, ctypes.c_double, i32, i32, _VP, _VP]
+    L.tf_lbm_term_norms.argtypes = [_VP, _VP, _VP]
     L.tf_lbm_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(_VP), i32, _VP]
     L.tf_lbm_batch_step.argtypes = [_VP, i64, _VP]
     L.tf_lbm_batch_get_launch.argtypes = [_VP, ctypes.POINTER(BatchLaunch)]
     L.tf_lbm_batch_set_launch.argtypes = [_VP, ctypes.POINTER(BatchLaunch)]
     L.tf_lbm_batch_tune.argtypes = [_VP, i32, ctypes.POINTER(BatchLaunch), _VP]
-    L.tf_lbm_batch_diagnostics.argtypes = [_VP, ctypes.c_double, _VP, _VP]
+    L.tf_lbm_batch_diagnostics.argtypes = [_VP, ctypes.c_double, i32, i32, _VP, _VP]
     L.tf_lbm_batch_items.argtypes = [_VP]
     L.tf_lbm_batch_items.restype = i32
     L.tf_lbm_batch_destroy.argtypes = [_VP]
@@ -240,8 +242,14 @@ def tf_lbm_tune(handle: int, trial_steps: int = 16, stream: int = 0) -> Launch:
     return out
 
 
-def tf_lbm_diagnostics(handle: int, h_wet: float, out: int, stream: int = 0) -> None:
-    _check(lib().tf_lbm_diagnostics(_VP(handle), float(h_wet), _VP(out), _VP(stream)), _VP(handle))
+def tf_lbm_diagnostics(handle: int, h_wet: float, mode_x: int, mode_y: int, out: int,
+                       stream: int = 0) -> None:
+    _check(lib().tf_lbm_diagnostics(_VP(handle), float(h_wet), int(mode_x), int(mode_y), _VP(out),
+                                    _VP(stream)), _VP(handle))
+
+
+def tf_lbm_term_norms(handle: int, out: int, stream: int = 0) -> None:
+    _check(lib().tf_lbm_term_norms(_VP(handle), _VP(out), _VP(stream)), _VP(handle))
 
 
 def _bcheck(rc: int, batch=None):
@@ -279,8 +287,10 @@ def tf_lbm_batch_tune(batch: int, trial_steps: int = 16, stream: int = 0) -> Bat
     return out
 
 
-def tf_lbm_batch_diagnostics(batch: int, h_wet: float, out: int, stream: int = 0) -> None:
-    _bcheck(lib().tf_lbm_batch_diagnostics(_VP(batch), float(h_wet), _VP(out), _VP(stream)), _VP(batch))
+def tf_lbm_batch_diagnostics(batch: int, h_wet: float, mode_x: int, mode_y: int, out: int,
+                             stream: int = 0) -> None:
+    _bcheck(lib().tf_lbm_batch_diagnostics(_VP(batch), float(h_wet), int(mode_x), int(mode_y), _VP(out),
+                                           _VP(stream)), _VP(batch))
 
 
 def tf_lbm_batch_items(batch: int) -> int:

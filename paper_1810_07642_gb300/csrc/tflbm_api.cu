@@ -462,6 +462,7 @@ void tf_lbm_destroy(tf_lbm_handle* H)
     if (H->diag) cudaFree(H->diag);
     if (H->adj) cudaFree(H->adj);
     if (H->dscr) cudaFree(H->dscr);
+    if (H->tscr) cudaFree(H->tscr);
     delete H;
 }
 

@@ -318,14 +318,17 @@ __device__ __forceinline__ Pops<T, SM> pops_of(const BatchDomain<T>& D, int pari
     return P;
 }
 
-// Film diagnostics of domain blockIdx.y of a table: compensated sums of h
-// over the lattice and, over the wetted nodes (h > h_wet), of h, j_x, j_y and
-// 1; and the largest h.  Block b writes kDiagPartial doubles at
+// Film diagnostics of domain blockIdx.y of a table (compensated sums in
+// double): [0] h over the lattice; over the wetted nodes (h > h_wet) [1] h,
+// [2] j_x, [3] j_y, [4] 1, [5] h cos(2 pi x / nx), [6] h sin(2 pi x / nx),
+// [7] h cos(2 pi y / ny), [8] h sin(2 pi y / ny); over the lattice
+// [9] h cos(phi), [10] h sin(phi) with phi = 2 pi (mx x / nx + my y / ny);
+// and the largest h.  Block b writes kDiagPartial doubles at
 // partials[(domain * gridDim.x + b) * kDiagPartial].
 constexpr int kDiagPartial = 2 * kDiagSums + 1;
 template <typename T, typename SM>
 __global__ void __launch_bounds__(kMassThreads) k_diag_partial(const BatchDomain<T>* __restrict__ doms, int parity,
-                                                               double h_wet, double* partials)
+                                                               double h_wet, int mx, int my, double* partials)
 {
     const BatchDomain<T>& D = doms[blockIdx.y];
     const Pops<T, SM> P = pops_of<T, SM>(D, parity);
@@ -335,18 +338,33 @@ __global__ void __launch_bounds__(kMassThreads) k_diag_partial(const BatchDomain
     for (int k = 0; k < kDiagSums; ++k) a[k] = Comp{0.0, 0.0};
     double hmax = -INFINITY;
     const long long n = (long long)G.nx * G.ny;
+    // integer wave numbers reduced modulo the lattice, so phases stay exact
+    const long long kx = ((mx % G.nx) + G.nx) % G.nx, ky = ((my % G.ny) + G.ny) % G.ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % G.nx), y = (int)(i / G.nx);
         T v[9], hh, jx, jy;
-        pull_at(P, G, (int)(i % G.nx), (int)(i / G.nx), v);
+        pull_at(P, G, x, y, v);
         moments9(v, hh, jx, jy);
         const double h = (double)hh;
         comp_add(a[0], h);
+        const double q = (double)((kx * x) % G.nx) / G.nx + (double)((ky * y) % G.ny) / G.ny;
+        double sp, cp;
+        sincospi(2.0 * q, &sp, &cp);
+        comp_add(a[9], h * cp);
+        comp_add(a[10], h * sp);
         if (h > h_wet) {
             comp_add(a[1], h);
             comp_add(a[2], (double)jx);
             comp_add(a[3], (double)jy);
             a[4].s += 1.0;  // exact below 2^53
+            double sx, cx, sy, cy;
+            sincospi(2.0 * x / G.nx, &sx, &cx);
+            sincospi(2.0 * y / G.ny, &sy, &cy);
+            comp_add(a[5], h * cx);
+            comp_add(a[6], h * sx);
+            comp_add(a[7], h * cy);
+            comp_add(a[8], h * sy);
         }
         hmax = fmax(hmax, h);
     }
@@ -364,7 +382,8 @@ __global__ void __launch_bounds__(kMassThreads) k_diag_partial(const BatchDomain
 }
 
 // One block per domain: reduce the partials of its nb blocks into
-// out[domain * kDiagOut ..]: the five sums, then the maximum.
+// out[domain * kDiagOut ..] in the order of tf_lbm_diag: sums 0..4, the
+// maximum, sums 5..10.
 __global__ void __launch_bounds__(kMassThreads) k_diag_final(const double* __restrict__ partials, int nb,
                                                              double* out)
 {
@@ -377,12 +396,113 @@ __global__ void __launch_bounds__(kMassThreads) k_diag_final(const double* __res
             a.c += p[i * kDiagPartial + 2 * k + 1];
         }
         const Comp b = block_sum(a);
-        if (threadIdx.x == 0) o[k] = b.s + b.c;
+        if (threadIdx.x == 0) o[k < 5 ? k : k + 1] = b.s + b.c;
     }
     double m = -INFINITY;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, p[i * kDiagPartial + 2 * kDiagSums]);
     m = block_max(m);
-    if (threadIdx.x == 0) o[kDiagSums] = m;
+    if (threadIdx.x == 0) o[5] = m;
+}
+
+// ---- term balance of the appendix (Eq. magnitude): fields h, j, p, div j
+template <typename T, typename SM>
+__global__ void k_tn_fields(Pops<T, SM> P, T* hb, T* jxb, T* jyb, Geom G)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= G.nx) return;
+    T v[9], hh, jx, jy;
+    pull_at(P, G, x, y, v);
+    moments9(v, hh, jx, jy);
+    const long long i = (long long)y * G.nx + x;
+    hb[i] = hh;
+    jxb[i] = jx;
+    jyb[i] = jy;
+}
+
+// d/dx and d/dy of a field with the stencil of Eq. (derivative)
+template <typename T>
+struct Stencil {
+    const T* f;
+    Geom G;
+    int x, y, xm, xp, ym, yp;
+    __device__ Stencil(const T* f_, const Geom& G_, int x_, int y_) : f(f_), G(G_), x(x_), y(y_)
+    {
+        xm = wrapi(x - 1, G.nx);
+        xp = wrapi(x + 1, G.nx);
+        ym = wrapi(y - 1, G.ny);
+        yp = wrapi(y + 1, G.ny);
+    }
+    __device__ T at(int yy, int xx) const { return f[(long long)yy * G.nx + xx]; }
+    __device__ T dx() const
+    {
+        return (at(y, xp) - at(y, xm)) / T(3) + (at(yp, xp) - at(yp, xm) + at(ym, xp) - at(ym, xm)) / T(12);
+    }
+    __device__ T dy() const
+    {
+        return (at(yp, x) - at(ym, x)) / T(3) + (at(yp, xp) - at(ym, xp) + at(yp, xm) - at(ym, xm)) / T(12);
+    }
+    // Eq. (n_laplace) with the reading (1/6)[4 sum_axis + sum_diag - 20 phi]
+    __device__ T lap() const
+    {
+        const T axis = at(y, xm) + at(y, xp) + at(ym, x) + at(yp, x);
+        const T diag = at(ym, xm) + at(ym, xp) + at(yp, xm) + at(yp, xp);
+        return (T(4) * axis + diag - T(20) * at(y, x)) / T(6);
+    }
+};
+
+template <typename T>
+__global__ void k_tn_div(const T* __restrict__ jx, const T* __restrict__ jy, T* div, Geom G)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= G.nx) return;
+    div[(long long)y * G.nx + x] = Stencil<T>(jx, G, x, y).dx() + Stencil<T>(jy, G, x, y).dy();
+}
+
+// Sums of squares of the x-components of -h d_x p, -nu alpha(h) u_x and
+// nu lap(j_x) + 2 nu d_x(div j) (three (s, c) pairs per block).
+template <typename T>
+__global__ void __launch_bounds__(kMassThreads) k_tn_terms(const T* __restrict__ hb, const T* __restrict__ jxb,
+                                                           const T* __restrict__ pb, const T* __restrict__ db,
+                                                           Geom G, Consts<T> C, double* partials)
+{
+    Comp a[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    const long long n = (long long)G.nx * G.ny;
+    const double nu = (double)C.nu6 / 6.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % G.nx), y = (int)(i / G.nx);
+        const double h = (double)hb[i], jx = (double)jxb[i], d = (double)C.delta;
+        const double tp = -h * (double)Stencil<T>(pb, G, x, y).dx();
+        // nu alpha(h) u_x = 6 nu j_x / (2 h^2 + 6 delta h + 3 delta^2), Eqs. (forcefric, alphafric)
+        const double tf = -6.0 * nu * jx / (2.0 * h * h + 6.0 * d * h + 3.0 * d * d);
+        const double td = nu * (double)Stencil<T>(jxb, G, x, y).lap() + 2.0 * nu * (double)Stencil<T>(db, G, x, y).dx();
+        comp_add(a[0], tp * tp);
+        comp_add(a[1], tf * tf);
+        comp_add(a[2], td * td);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const Comp b = block_sum(a[k]);
+        if (threadIdx.x == 0) {
+            partials[2 * (k * gridDim.x + blockIdx.x)] = b.s;
+            partials[2 * (k * gridDim.x + blockIdx.x) + 1] = b.c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMassThreads) k_tn_final(const double* __restrict__ partials, int nb, double n,
+                                                           double* out)
+{
+    for (int k = 0; k < 3; ++k) {
+        Comp a{0.0, 0.0};
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            comp_add(a, partials[2 * (k * nb + i)]);
+            a.c += partials[2 * (k * nb + i) + 1];
+        }
+        const Comp b = block_sum(a);
+        if (threadIdx.x == 0) out[k] = sqrt((b.s + b.c) / n);
+    }
 }
 
 // Smallest of n values (NaNs ignored; +inf when there is none).
@@ -528,12 +648,30 @@ cudaError_t mass_t(const StoreDesc& D, const void* f, const Geom& G, double* par
 }
 
 template <typename T, typename SM>
-cudaError_t diag_t(const void* doms, int ndom, int parity, double h_wet, double* partials, int nb, double* out,
-                   cudaStream_t st)
+cudaError_t diag_t(const void* doms, int ndom, int parity, double h_wet, int mx, int my, double* partials, int nb,
+                   double* out, cudaStream_t st)
 {
     k_diag_partial<T, SM><<<dim3(nb, ndom), kMassThreads, 0, st>>>((const BatchDomain<T>*)doms, parity, h_wet,
-                                                                  partials);
+                                                                  mx, my, partials);
     k_diag_final<<<ndom, kMassThreads, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+template <typename T, typename SM>
+cudaError_t term_norms_t(const StoreDesc& D, const void* f, const void* kappa, const Geom& G, const Consts<T>& C,
+                         void* scratch, double* partials, int nb, double* out, cudaStream_t st)
+{
+    const long long n = (long long)G.nx * G.ny;
+    T* hb = (T*)scratch;
+    T* jxb = hb + n;
+    T* jyb = jxb + n;
+    T* pb = jyb + n;
+    T* db = pb + n;
+    k_tn_fields<T, SM><<<grid2d(G, 128), 128, 0, st>>>(make_pops<T, SM>(f, G, D), hb, jxb, jyb, G);
+    k_pf_p<T><<<grid2d(G, 128), 128, 0, st>>>(hb, (const T*)kappa, pb, G, C);
+    k_tn_div<T><<<grid2d(G, 128), 128, 0, st>>>(jxb, jyb, db, G);
+    k_tn_terms<T><<<nb, kMassThreads, 0, st>>>(hb, jxb, pb, db, G, C, partials);
+    k_tn_final<<<1, kMassThreads, 0, st>>>(partials, nb, (double)n, out);
     return cudaGetLastError();
 }
 
@@ -614,14 +752,29 @@ cudaError_t aux_mass(const StoreDesc& D, const void* f, const Geom& G, double* p
     TFLBM_DISPATCH(D, (mass_t<T, SM>(D, f, G, partials, nblocks, result, st)))
 }
 
-cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, double* partials, int nb,
-                     double* out, cudaStream_t st)
+cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, int mx, int my,
+                     double* partials, int nb, double* out, cudaStream_t st)
 {
     switch (store) {
-        case kStoreF32: return diag_t<float, float>(doms, ndom, parity, h_wet, partials, nb, out, st);
-        case kStoreF64: return diag_t<double, double>(doms, ndom, parity, h_wet, partials, nb, out, st);
-        case kStoreF16: return diag_t<float, __half>(doms, ndom, parity, h_wet, partials, nb, out, st);
-        case kStoreBF16: return diag_t<float, __nv_bfloat16>(doms, ndom, parity, h_wet, partials, nb, out, st);
+        case kStoreF32: return diag_t<float, float>(doms, ndom, parity, h_wet, mx, my, partials, nb, out, st);
+        case kStoreF64: return diag_t<double, double>(doms, ndom, parity, h_wet, mx, my, partials, nb, out, st);
+        case kStoreF16: return diag_t<float, __half>(doms, ndom, parity, h_wet, mx, my, partials, nb, out, st);
+        case kStoreBF16:
+            return diag_t<float, __nv_bfloat16>(doms, ndom, parity, h_wet, mx, my, partials, nb, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t aux_term_norms(const StoreDesc& D, const void* f, const void* kappa, const Geom& G,
+                           const Consts<float>* C32, const Consts<double>* C64, void* scratch, double* partials,
+                           int nb, double* out, cudaStream_t st)
+{
+    switch (D.store) {
+        case kStoreF32: return term_norms_t<float, float>(D, f, kappa, G, *C32, scratch, partials, nb, out, st);
+        case kStoreF64: return term_norms_t<double, double>(D, f, kappa, G, *C64, scratch, partials, nb, out, st);
+        case kStoreF16: return term_norms_t<float, __half>(D, f, kappa, G, *C32, scratch, partials, nb, out, st);
+        case kStoreBF16:
+            return term_norms_t<float, __nv_bfloat16>(D, f, kappa, G, *C32, scratch, partials, nb, out, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -370,7 +370,7 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
     return finish(TF_LBM_OK);
 }
 
-int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, void* out, void* stream)
+int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, int32_t mode_x, int32_t mode_y, void* out, void* stream)
 {
     if (!H) {
         set_thread_error("handle is NULL");
@@ -398,8 +398,36 @@ int tf_lbm_diagnostics(tf_lbm_handle* H, double h_wet, void* out, void* stream)
     else d32 = domain_of<float>(H, H->cur, H->kappa);
     cudaError_t e = cudaMemcpyAsync(H->dscr, rec, domain_bytes(H->dbl), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return handle_cuda_fail(H, e, "cudaMemcpyAsync diagnostics record");
-    e = aux_diag(H->desc.store, H->dscr, 1, 0, h_wet, (double*)((char*)H->dscr + tab), nb, (double*)out, st);
+    e = aux_diag(H->desc.store, H->dscr, 1, 0, h_wet, mode_x, mode_y, (double*)((char*)H->dscr + tab), nb,
+                 (double*)out, st);
     if (e != cudaSuccess) return handle_cuda_fail(H, e, "diagnostics kernels");
+    return TF_LBM_OK;
+}
+
+int tf_lbm_term_norms(tf_lbm_handle* H, void* out, void* stream)
+{
+    if (!H) {
+        set_thread_error("handle is NULL");
+        return TF_LBM_ERR_ARG;
+    }
+    int rc = handle_check_dev_ptr(H, out, "out", false);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = (long long)H->G.nx * H->G.ny;
+    const int nb = (int)std::min<long long>(kSumBlocks, std::max<long long>(1, n / (256LL * 16)));
+    const size_t fields = (5 * n * H->esize + 255) / 256 * 256;
+    if (!H->tscr) {
+        cudaError_t e = cudaMalloc(&H->tscr, fields + 6 * sizeof(double) * kSumBlocks);
+        if (e != cudaSuccess) {
+            H->tscr = nullptr;
+            return handle_cuda_fail(H, e, "cudaMalloc term-norm scratch");
+        }
+    }
+    const Consts<float> c32 = make_consts<float>(H);
+    const Consts<double> c64 = make_consts<double>(H);
+    cudaError_t e = aux_term_norms(H->desc, H->buf[H->cur], H->kappa, H->G, &c32, &c64, H->tscr,
+                                   (double*)((char*)H->tscr + fields), nb, (double*)out, st);
+    if (e != cudaSuccess) return handle_cuda_fail(H, e, "term-norm kernels");
     return TF_LBM_OK;
 }
 
@@ -636,7 +664,8 @@ int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch*
     return finish(TF_LBM_OK);
 }
 
-int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, void* out, void* stream)
+int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, int32_t mode_x, int32_t mode_y, void* out,
+                             void* stream)
 {
     if (!B) return bfail(nullptr, TF_LBM_ERR_ARG, "batch is NULL");
     if (!out) return bfail(B, TF_LBM_ERR_ARG, "out must not be NULL");
@@ -650,8 +679,8 @@ int tf_lbm_batch_diagnostics(tf_lbm_batch* B, double h_wet, void* out, void* str
     cudaStream_t st = (cudaStream_t)stream;
     int rc = sync_table(B, st);
     if (rc) return rc;
-    BCK(B, aux_diag(B->store, B->doms, (int)B->hs.size(), B->phase, h_wet, B->dpart, kDiagBlocksPerDomain,
-                    (double*)out, st),
+    BCK(B, aux_diag(B->store, B->doms, (int)B->hs.size(), B->phase, h_wet, mode_x, mode_y, B->dpart,
+                    kDiagBlocksPerDomain, (double*)out, st),
         "diagnostics kernels");
     return TF_LBM_OK;
 }

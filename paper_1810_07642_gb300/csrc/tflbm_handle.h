@@ -38,6 +38,7 @@ struct tf_lbm_handle {
     std::string err;
     void* adj = nullptr;       // adjoint scratch (lazy): 10 fields of the compute type
     void* dscr = nullptr;      // diagnostics scratch (lazy): one BatchDomain entry + partial sums
+    void* tscr = nullptr;      // term-norm scratch (lazy): 5 fields + partial sums
 };
 
 

@@ -123,13 +123,20 @@ cudaError_t aux_get_state(const StoreDesc& D, const void* f, double* out, const 
 cudaError_t aux_set_state(const StoreDesc& D, void* f, const double* in, const Geom& G, cudaStream_t st);
 // post-streaming populations in the compute type, [9][ny][nx]
 // Film diagnostics of each domain of a BatchDomain table (buffer `parity`):
-// out[d * kDiagOut + k] = sum h, sum of h / j_x / j_y / 1 over nodes with
-// h > h_wet, max h.  partials holds ndom * nb * (2 kDiagSums + 1) doubles.
-constexpr int kDiagSums = 5;
+// out[d * kDiagOut ..] = the fields of tf_lbm_diag (wetted nodes: h > h_wet;
+// Fourier sums at the integer modes (mx, my)).  partials holds
+// diag_partials(ndom, nb) doubles.
+constexpr int kDiagSums = 11;
 constexpr int kDiagOut = kDiagSums + 1;
 inline size_t diag_partials(int ndom, int nb) { return (size_t)ndom * nb * (2 * kDiagSums + 1); }
-cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, double* partials, int nb,
-                     double* out, cudaStream_t st);
+cudaError_t aux_diag(int store, const void* doms, int ndom, int parity, double h_wet, int mx, int my,
+                     double* partials, int nb, double* out, cudaStream_t st);
+// L2 norms (appendix, Eq. magnitude) of the x-components of the pressure,
+// friction and dissipation terms into out[0..2]; scratch holds 5 fields of
+// the compute type, partials 6 * nb doubles.
+cudaError_t aux_term_norms(const StoreDesc& D, const void* f, const void* kappa, const Geom& G,
+                           const Consts<float>* C32, const Consts<double>* C64, void* scratch, double* partials,
+                           int nb, double* out, cudaStream_t st);
 cudaError_t aux_export_state(const StoreDesc& D, const void* f, void* out, const Geom& G, cudaStream_t st);
 cudaError_t aux_kappa(bool dbl, void* kappa, const void* theta, int nx, int ny, int ne, int me,
                       double hstar, cudaStream_t st);

@@ -125,12 +125,20 @@ class ThinFilm:
         l = L.tf_lbm_tune(self.handle, trial_steps, self._st)
         return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, pipeline=l.pipeline)
 
-    def diagnostics(self, h_wet: float, out=None):
-        """Film diagnostics of the current state (a float64 tensor of the six
-        tf_lbm_diag fields, on the device; no host synchronisation)."""
+    def diagnostics(self, h_wet: float, mode=(1, 0), out=None):
+        """Film diagnostics of the current state: a float64 device tensor of
+        the tf_lbm_diag fields (_lib.DIAG_FIELDS), no host synchronisation."""
         if out is None:
             out = torch.empty(len(L.DIAG_FIELDS), dtype=torch.float64, device=self.device)
-        L.tf_lbm_diagnostics(self.handle, h_wet, out.data_ptr(), self._st)
+        L.tf_lbm_diagnostics(self.handle, h_wet, mode[0], mode[1], out.data_ptr(), self._st)
+        return out
+
+    def term_norms(self, out=None):
+        """L2 norms of the pressure, friction and dissipation terms (x
+        components) of the paper's appendix, as a float64 device tensor."""
+        if out is None:
+            out = torch.empty(3, dtype=torch.float64, device=self.device)
+        L.tf_lbm_term_norms(self.handle, out.data_ptr(), self._st)
         return out
 
     def close(self):
@@ -186,12 +194,12 @@ class FilmBatch:
         l = L.tf_lbm_batch_tune(self.batch, trial_steps, self._st)
         return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue)
 
-    def diagnostics(self, h_wet: float, out=None):
-        """(count, 6) float64 device tensor of tf_lbm_diag rows, one per film."""
+    def diagnostics(self, h_wet: float, mode=(1, 0), out=None):
+        """(count, 12) float64 device tensor of tf_lbm_diag rows, one per film."""
         if out is None:
             out = torch.empty((len(self.films), len(L.DIAG_FIELDS)), dtype=torch.float64,
                               device=self.device)
-        L.tf_lbm_batch_diagnostics(self.batch, h_wet, out.data_ptr(), self._st)
+        L.tf_lbm_batch_diagnostics(self.batch, h_wet, mode[0], mode[1], out.data_ptr(), self._st)
         return out
 
     def close(self):
