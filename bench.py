@@ -338,6 +338,87 @@ def batched_sweep(steps: int = 30000, timed: int = 400):
     return out
 
 
+def small_workloads():
+    """Configs 1 and 2, measured with the device diagnostics.
+
+    Rayleigh-Taylor (128^2, g = -1e-4, 2000 steps, FP64 and FP32): growth
+    rate of the seeded mode fitted from its Fourier amplitude over steps
+    100..2000, beside Eq. (RTgrowth)'s continuum rate (the scheme's explicit
+    friction lowers it, see the design notes), mass drift, and MLUPS of this
+    L2-resident, launch-bound lattice (graph-replayed steps).
+    Sessile drop (512^2, r_b = 120, h_d = 20, theta = 20 deg, 50k steps FP32,
+    delta in {0, 1, 2}): contact radius every 2500 steps and the final
+    apparent angle (threshold h* + 0.01 h_d); delta = 0 diverges (explicit
+    friction on the precursor) and is reported with the step it was found."""
+    import torch
+    from paper_1810_07642_gb300 import diagnostics as D
+    from paper_1810_07642_gb300 import inputs
+    from paper_1810_07642_gb300.film import ThinFilm
+    out = {"rayleigh_taylor": {}, "sessile_drop": {}}
+    h0, th, p = inputs.rayleigh_taylor(128, mode=1, g=-1e-4)
+    k = 2 * math.pi / 128
+    nu = (p["tau"] - 0.5) / 3
+    cont = (1e-4 / (3 * nu)) * (k * k - (p["gamma"] / 1e-4) * k ** 4)
+    for dt in ("f64", "f32"):
+        sim = ThinFilm(p, h0, th, dtype=dt)
+        m0 = sim.mass()
+        ts, la = [], []
+        for t in range(0, 2001, 100):
+            if t:
+                sim.step(100)
+            if t >= 100:
+                ts.append(t)
+                la.append(math.log(D.mode_amplitude(sim.diagnostics(0.0, mode=(1, 0)).cpu().numpy(),
+                                                    128, 128)))
+        sig = float(np.polyfit(ts, la, 1)[0])
+        m1 = sim.mass()
+        launch = sim.tune(16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sim.step(128)
+        e0.record()
+        sim.step(4096)
+        e1.record()
+        torch.cuda.synchronize()
+        out["rayleigh_taylor"][dt] = {"sigma_fit_per_step": sig, "sigma_eq_rtgrowth": cont,
+                                      "mass_rel_drift_2000": abs(m1 - m0) / m0,
+                                      "mlups_l2_resident_launch_bound": 128 * 128 * 4096 /
+                                      e0.elapsed_time(e1) / 1e3, "tuned_launch": launch}
+        sim.close()
+    for delta in (0.0, 1.0, 2.0):
+        h0, th, p = inputs.sessile_drop(512, rb=120.0, hd=20.0, theta_deg=20.0, delta=delta)
+        p = dict(p, theta_uniform=math.radians(20.0))
+        sim = ThinFilm(p, h0, None)
+        launch = sim.tune(16)
+        m0 = sim.mass()
+        curve, status, t = [], 0, 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        while t < 50000:
+            e0.record()
+            sim.step(2500)
+            e1.record()
+            t += 2500
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            status = sim.check()
+            if status:
+                break
+            hd = sim.diagnostics(p["hstar"]).cpu().numpy()[5] - p["hstar"]
+            g = D.drop(sim.diagnostics(p["hstar"] + 0.01 * hd).cpu().numpy(), p["hstar"], 512, 512,
+                       p["tau"], p["gamma"])
+            curve.append([t, round(g["contact_radius"], 3), round(math.degrees(g["theta"]), 3)])
+        rec = {"status": status, "steps": t, "mlups": 512 * 512 * t / ms / 1e3, "tuned_launch": launch}
+        if status:
+            rec["diverged_by_step"] = t
+        else:
+            rec["r_theta_every_2500"] = curve
+            rec["theta_final_deg"] = curve[-1][2]
+            rec["mass_rel_drift"] = abs(sim.mass() - m0) / m0
+        out["sessile_drop"][f"delta_{delta:g}"] = rec
+        sim.close()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
     2048 x R periodic band of the workload, R sized to fit a few minutes."""
@@ -478,6 +559,7 @@ def run_tflbm(args):
         extras["storage"] = storage_variants()
         extras["adjoint"] = adjoint_cost()
         extras["batched_sweep"] = batched_sweep()
+        extras["small_workloads"] = small_workloads()
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
