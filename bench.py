@@ -485,7 +485,7 @@ def run_tflbm(args):
     h0, th, p = inputs.patterned_dewetting(N_SIDE, seed=rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = ThinFilm(p, h0, th, stream=stream)
+        sim = ThinFilm(p, h0, th, dtype=args.storage, stream=stream)
     launch = sim.launch
     nodes = N_SIDE * N_SIDE
 
@@ -521,9 +521,10 @@ def run_tflbm(args):
     # dominant kernel: the fused step, one launch per step, launches back to
     # back, so its average duration is the timed region over K
     kern_s = t_local / args.steps
-    achieved = BYTES_PER_LU * nodes / kern_s / 1e9
+    bpl = BYTES_PER_LU if args.storage == "f32" else 44  # 16-bit: 2 x (4 + 8 x 2) + 4
+    achieved = bpl * nodes / kern_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic, prof = profiled_traffic()
+    traffic, prof = profiled_traffic() if args.storage == "f32" else (None, None)
 
     # end to end through the public API with host buffers (pinned)
     h_host = torch.from_numpy(np.asarray(h0, np.float32)).pin_memory()
@@ -535,7 +536,7 @@ def run_tflbm(args):
     with torch.cuda.stream(stream):
         hd = h_host.to("cuda", non_blocking=True)
         thd = th_host.to("cuda", non_blocking=True)
-        sim2 = ThinFilm(p, hd, thd, stream=stream)
+        sim2 = ThinFilm(p, hd, thd, dtype=args.storage, stream=stream)
         sim2.set_launch(**launch)
         sim2.step(args.steps)
         hres = sim2.moments(("h",))["h"]
@@ -555,7 +556,7 @@ def run_tflbm(args):
     cpu = oracle_cpu_baseline() if world == 1 else None
     clocks = clk.summary()
     extras = {}
-    if world == 1 and not args.skip_extras:
+    if world == 1 and not args.skip_extras and args.storage == "f32":
         extras["storage"] = storage_variants()
         extras["adjoint"] = adjoint_cost()
         extras["batched_sweep"] = batched_sweep()
@@ -567,11 +568,12 @@ def run_tflbm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "replicas": world,
                    "l2": "inputs larger than L2 (302 MB populations + 17 MB kappa > 129 MB): no flush",
-                   "launch": launch, "bytes_per_lu": BYTES_PER_LU},
+                   "launch": launch, "bytes_per_lu": bpl, "storage": args.storage},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_step<float,float,OMEGA1,KFIELD>",
+                     "kernel": {"f32": "k_step<float,float,...>", "f16": "k_step<__half,float,...>",
+                                "bf16": "k_step<__nv_bfloat16,float,...>"}[args.storage],
                      "kernel_ms": kern_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -670,6 +672,8 @@ def main():
     ap.add_argument("--workload", default="patterned", choices=["patterned", "sweep"],
                     help="patterned: the 2048^2 dewetting run (default); sweep: the batched "
                          "64-domain sliding-drop sweep as the timed step")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage of the patterned workload (arithmetic is FP32)")
     ap.add_argument("--batch-launch", default="",
                     help="sweep workload: block_x,rows,graph_chunk,queue instead of autotuning")
     ap.add_argument("--skip-extras", action="store_true",

@@ -109,9 +109,12 @@ typedef struct tf_lbm_handle tf_lbm_handle;
  *   rows:    lattice rows marched by one CTA (>= 1);
  *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
  *            otherwise an even number >= 2);
- *   pipeline: 1 = every thread loads its own populations, one row ahead
- *            (default); 0 = row segments streamed into shared memory by
- *            bulk copies four rows ahead (needs nx a multiple of 8, >= 16).
+ *   pipeline: 1 = every thread loads its own populations into registers,
+ *            one row ahead (default); 2 = every thread copies its own
+ *            populations into shared memory by asynchronous copies, two
+ *            rows ahead (TF_LBM_F32 and TF_LBM_F64 only); 0 = row segments
+ *            streamed into shared memory by bulk copies four rows ahead
+ *            (needs nx a multiple of 8, >= 16).
  * Results do not depend on rows, graph_chunk or pipeline. */
 typedef struct tf_lbm_launch {
     int32_t block_x;

@@ -436,8 +436,11 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     if (in->rows < 1 || in->rows > 65535) return fail(H, TF_LBM_ERR_ARG, "rows must be in [1, 65535]");
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
-    if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg)
-        return fail(H, TF_LBM_ERR_ARG, "pipeline must be 0 (bulk copies) or 1 (per-thread loads)");
+    if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg && in->pipeline != kPipeAsync)
+        return fail(H, TF_LBM_ERR_ARG,
+                    "pipeline must be 0 (bulk copies), 1 (per-thread loads) or 2 (per-thread async copies)");
+    if (in->pipeline == kPipeAsync && H->msize != H->esize)
+        return fail(H, TF_LBM_ERR_ARG, "the async-copy pipeline needs FP32 or FP64 storage");
     if (in->pipeline == kPipeTma && !tma_pipeline_ok(H->G.nx))
         return fail(H, TF_LBM_ERR_ARG, "the bulk-copy pipeline needs nx to be a multiple of 8 and >= 16");
     drop_graphs(H);

@@ -17,6 +17,7 @@ struct Geom {
 // or per-thread global loads (any size).
 constexpr int kPipeTma = 0;
 constexpr int kPipeLdg = 1;
+constexpr int kPipeAsync = 2;  // per-thread cp.async staging (full-width storage only)
 inline bool tma_pipeline_ok(int nx) { return nx % 8 == 0 && nx >= 16; }
 
 // Status bit a kernel sets when an mbarrier wait gave up (tf_lbm_check).
@@ -47,7 +48,7 @@ struct Consts {
 struct Shape {
     int block_x;   // 64, 128, 256
     int rows;      // rows per CTA (band height)
-    int pipeline;  // kPipeTma or kPipeLdg
+    int pipeline;  // kPipeTma, kPipeLdg or kPipeAsync
 };
 
 // Storage of the 8 moving populations.

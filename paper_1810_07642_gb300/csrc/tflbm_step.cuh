@@ -315,17 +315,39 @@ __device__ __forceinline__ Band make_band(const Geom& G, int t, int strip, int b
     return b;
 }
 
+// Per-thread asynchronous global-to-shared copies (cp.async, 4 or 8 bytes).
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte elements");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------------------
 // Kernel 1: every thread loads its own nine pulled populations from global
-// memory, one row ahead of use (register prefetch).
-template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+// memory ahead of use: one row ahead into registers, or (ASYNC, full-width
+// storage only) kAsyncStages - 1 rows ahead into a private shared-memory
+// ring by cp.async, which keeps more bytes in flight without registers.
+constexpr int kAsyncStages = 3;
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD, bool ASYNC = false>
 __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* __restrict__ finm,
                                           T* __restrict__ fout0, SM* __restrict__ foutm,
                                           const T* __restrict__ kappa, const Geom& G, const Consts<T>& C,
                                           int strip, int band, int nbands)
 {
+    static_assert(!ASYNC || std::is_same<SM, T>::value, "async staging needs full-width storage");
     __shared__ T hsm[4][BX];  // h - href ring: slot t = column x0 - 2 + t
     __shared__ T psm[4][BX];  // p ring, same columns
+    // async ring: stage j % kAsyncStages holds the nine pulled values of row r(j)
+    __shared__ T stg[ASYNC ? kAsyncStages : 1][9][ASYNC ? BX : 1];
     const int t = threadIdx.x;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
     const Band B = make_band<BX>(G, t, strip, band, nbands);
@@ -335,9 +357,10 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
     const int x = wrap_index(B.x0 - 2 + t, nx);
     const int xm = wrap_index(x - 1, nx), xp = wrap_index(x + 1, nx);
 
-    // wrapped indices of rows r(k-1), r(k), r(k+1), r(k+2)
+    // wrapped indices of rows r(k-1), r(k), r(k+1), r(k+2), r(k+3)
     int wm1 = wrap_index(B.rstart - dir, ny), w0 = wrap_index(B.rstart, ny);
     int w1 = wrap_index(B.rstart + dir, ny), w2 = wrap_index(B.rstart + 2 * dir, ny);
+    int w3 = ASYNC ? wrap_index(B.rstart + 3 * dir, ny) : 0;
 
     T v[9];
     T kap_n = C.kappa_u;
@@ -352,7 +375,33 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
         const int below = (dir > 0 ? wb : wa) - w, above = (dir > 0 ? wa : wb) - w;
         pull9<SM, T>(fin0, finm, plane, r0 + x, r0 + xm, r0 + xp, below * pitch, above * pitch, C, v);
     };
-    if (B.hcol) pull_row(wm1, w0, w1);
+    // the same nine elements, copied asynchronously into stage st of the ring
+    // (one commit group per row, empty for threads that load nothing)
+    auto issue_row = [&](int st, int wb, int w, int wa) {
+        if (B.hcol) {
+            const int r0 = w * pitch;
+            const int dm = ((dir > 0 ? wb : wa) - w) * pitch, dp = ((dir > 0 ? wa : wb) - w) * pitch;
+            const int i0 = r0 + x, im = r0 + xm, ip = r0 + xp;
+            T(&d)[9][ASYNC ? BX : 1] = stg[st];
+            constexpr int E = sizeof(T);
+            cp_async<E>(&d[0][t], fin0 + i0);
+            cp_async<E>(&d[1][t], finm + im);
+            cp_async<E>(&d[2][t], finm + (plane + im + dm));
+            cp_async<E>(&d[3][t], finm + (2 * plane + i0 + dm));
+            cp_async<E>(&d[4][t], finm + (3 * plane + ip + dm));
+            cp_async<E>(&d[5][t], finm + (4 * plane + ip));
+            cp_async<E>(&d[6][t], finm + (5 * plane + ip + dp));
+            cp_async<E>(&d[7][t], finm + (6 * plane + i0 + dp));
+            cp_async<E>(&d[8][t], finm + (7 * plane + im + dp));
+        }
+        cp_async_commit();
+    };
+    if constexpr (ASYNC) {
+        issue_row(0, wm1, w0, w1);
+        issue_row(1, w0, w1, w2);
+    } else {
+        if (B.hcol) pull_row(wm1, w0, w1);
+    }
     if (KFIELD && B.pcol) kap_n = kappa[(long long)wm1 * nx + x];
 
     auto body = [&](auto stage_c, int k) {
@@ -362,6 +411,20 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
         constexpr int s3 = (s + 1) & 3;              // slot of row r(k-3)
         // ---- (A) h of row r(k); the loads of row r(k+1) go out before anything waits
         const T kap = kap_n;  // kappa of row r(k-1), loaded last step
+        if constexpr (ASYNC) {
+            // row r(k) has landed once at most one younger group is pending;
+            // then the stage of row r(k-1) (read last step) takes row r(k+2)
+            if (k <= R + 3) {
+                cp_async_wait<kAsyncStages - 2>();
+                if (B.hcol) {
+                    const int st = k % kAsyncStages;
+#pragma unroll
+                    for (int l = 0; l < 9; ++l) v[l] = stg[st][l][t];
+                }
+                if (k + 2 <= R + 3) issue_row((k + 2) % kAsyncStages, w1, w2, w3);
+                else cp_async_commit();
+            }
+        }
         if (B.hcol && k <= R + 3) {
             hsm[s][t] = sum9(v, erv[s]);
             jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
@@ -370,7 +433,7 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
 #pragma unroll
                 for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
             }
-            if (k + 1 <= R + 3) pull_row(w0, w1, w2);
+            if (!ASYNC && k + 1 <= R + 3) pull_row(w0, w1, w2);
             if (KFIELD && B.pcol) kap_n = kappa[(long long)w0 * nx + x];
         }
         __syncthreads();
@@ -390,8 +453,14 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
         wm1 = w0;
         w0 = w1;
         w1 = w2;
-        w2 += dir;
-        w2 = w2 == ny ? 0 : (w2 < 0 ? ny - 1 : w2);
+        if constexpr (ASYNC) {
+            w2 = w3;
+            w3 += dir;
+            w3 = w3 == ny ? 0 : (w3 < 0 ? ny - 1 : w3);
+        } else {
+            w2 += dir;
+            w2 = w2 == ny ? 0 : (w2 < 0 ? ny - 1 : w2);
+        }
     };
 
     const int last = R + 4;
@@ -407,13 +476,13 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
     }
 }
 
-template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
+template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD, bool ASYNC = false>
 __global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
 k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
        SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
-    step_band<SM, T, BX, OMEGA1, KFIELD>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
-                                         gridDim.y);
+    step_band<SM, T, BX, OMEGA1, KFIELD, ASYNC>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x,
+                                                blockIdx.y, gridDim.y);
 }
 
 // One batched step.  Each work item is one band of one strip of one domain;
@@ -730,6 +799,11 @@ cudaError_t launch_one(int pipeline, dim3 grid, const T* fin0, const SM* finm, T
             attr = true;
         }
         k_step_tma<SM, T, BX, OM1, KF><<<grid, BX, L::BYTES, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+    } else if constexpr (std::is_same<SM, T>::value) {
+        if (pipeline == kPipeAsync)
+            k_step<SM, T, BX, OM1, KF, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+        else
+            k_step<SM, T, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
     } else {
         k_step<SM, T, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
     }
@@ -795,6 +869,11 @@ int bps_one(int pipeline)
         cudaFuncSetAttribute(k_step_tma<SM, T, BX, OM1, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              L::BYTES);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tma<SM, T, BX, OM1, KF>, BX, L::BYTES);
+    } else if constexpr (std::is_same<SM, T>::value) {
+        if (pipeline == kPipeAsync)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, OM1, KF, true>, BX, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, OM1, KF>, BX, 0);
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<SM, T, BX, OM1, KF>, BX, 0);
     }

@@ -130,7 +130,9 @@ def test_parity_patterned_dewetting_256_fp32():
                                    dict(block_x=128, rows=64), dict(block_x=256, rows=17),
                                    dict(block_x=128, rows=3, graph_chunk=4),
                                    dict(block_x=64, rows=9, pipeline=0),
-                                   dict(block_x=128, rows=33, pipeline=0)])
+                                   dict(block_x=128, rows=33, pipeline=0),
+                                   dict(block_x=64, rows=1, pipeline=2),
+                                   dict(block_x=128, rows=29, pipeline=2, graph_chunk=4)])
 def test_launch_shape_does_not_change_results(shape):
     """Every node does the same arithmetic in the same order whatever the band
     height or graph chunking, so with the same CTA width and load pipeline
@@ -328,6 +330,26 @@ def test_parity_bulk_copy_pipeline(dtype, nx, ny):
     p.update(tau=0.9 if dtype == "f64" else 1.0, g=2e-4, gx_body=2e-5, delta=1.0)
     r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=0))
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (130, 70), (3, 3), (2, 1), (200, 2)])
+@pytest.mark.parametrize("rows", [1, 2, 16])
+def test_parity_async_copy_pipeline(dtype, nx, ny, rows):
+    """The async-copy kernel (pipeline 2) against the oracle, including bands
+    of one and two rows, where the three-stage ring wraps every step."""
+    h0, th, p = inputs.small_random(nx, ny, seed=nx * 3 + ny, amp=0.05)
+    p.update(tau=0.9 if dtype == "f64" else 1.0, g=2e-4, gx_body=2e-5, delta=1.0)
+    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=2, rows=rows))
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+
+
+def test_async_copy_pipeline_needs_full_width_storage():
+    h0, th, p = inputs.small_random(16, 16, seed=1)
+    sim = ThinFilm(p, h0, th, dtype="f16")
+    with pytest.raises(L.TfLbmError) as e:
+        sim.set_launch(pipeline=2)
+    assert "FP32 or FP64" in str(e.value)
 
 
 def test_invalid_arguments_are_rejected():
