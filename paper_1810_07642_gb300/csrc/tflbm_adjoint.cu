@@ -24,8 +24,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
+#include "tflbm_adjoint_march.cuh"
 #include "tflbm_handle.h"
 
 namespace tflbm {
@@ -264,6 +266,52 @@ cudaError_t adjoint_step_dispatch(tf_lbm_handle* H, const void* f, const void* a
     return H->dbl ? adjoint_t<double>(H, f, an, a, gk, st) : adjoint_t<float>(H, f, an, a, gk, st);
 }
 
+namespace {
+
+template <typename SM, typename T, int BX>
+cudaError_t march_t(tf_lbm_handle* H, const void* fin, const void* an, void* a, void* gk, int rows,
+                    cudaStream_t st)
+{
+    const Geom& G = H->G;
+    const T* f0 = (const T*)fin;
+    const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(T));
+    int bands = (G.ny + rows - 1) / rows;
+    if (bands > 65535) bands = 65535;
+    const dim3 grid((G.nx + BX - 9) / (BX - 8), bands);
+    k_adjoint_march<SM, T, BX><<<grid, BX, 0, st>>>(f0, fm, (const T*)an, (T*)a, (T*)gk, (const T*)H->kappa, G,
+                                                    make_consts<T>(H));
+    return cudaGetLastError();
+}
+
+template <typename SM, typename T, int BX>
+int march_rows(const tf_lbm_handle* H)
+{
+    int occ = 0, sms = sm_count();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_march<SM, T, BX>, BX, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int strips = (H->G.nx + BX - 9) / (BX - 8);
+    const int bands = std::max(1, std::max(occ, 1) * sms / strips);
+    return std::max(8, (H->G.ny + bands - 1) / bands);
+}
+
+}  // namespace
+
+// Fused adjoint step from the raw buffer whose pull is f(t).
+cudaError_t adjoint_march_dispatch(tf_lbm_handle* H, const void* fin, const void* an, void* a, void* gk,
+                                   cudaStream_t st)
+{
+    switch (H->desc.store) {
+        case kStoreF32: return march_t<float, float, 128>(H, fin, an, a, gk, march_rows<float, float, 128>(H), st);
+        case kStoreF64: return march_t<double, double, 64>(H, fin, an, a, gk, march_rows<double, double, 64>(H), st);
+        case kStoreF16: return march_t<__half, float, 128>(H, fin, an, a, gk, march_rows<__half, float, 128>(H), st);
+        case kStoreBF16:
+            return march_t<__nv_bfloat16, float, 128>(H, fin, an, a, gk, march_rows<__nv_bfloat16, float, 128>(H), st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace tflbm
 
 // ---------------------------------------------------------------- the tape
@@ -275,16 +323,16 @@ struct tf_lbm_tape {
     int nck = 0;                   // checkpoints: states at 0, K, 2K, ...
     size_t state_bytes = 0;        // one raw population buffer
     void* ck = nullptr;            // nck raw buffers, then the final state
-    void* seg = nullptr;           // every + 1 exported states (compute type)
+    void* seg = nullptr;           // every raw population buffers: the states of one segment
     void* abuf = nullptr;          // 2 adjoint states
     void* gk = nullptr;            // dL/dkappa
     void* h0 = nullptr;            // copy of h0 (compute type)
     void* theta = nullptr;         // copy of theta or null (uniform)
     int64_t t0 = 0;                // handle time when the forward started
     bool forwarded = false;
-    // CUDA graphs of one full segment: recompute (by starting buffer) and
-    // the adjoint chain (by starting adjoint buffer)
-    cudaGraphExec_t g_rec[2] = {nullptr, nullptr};
+    // CUDA graphs of one full segment: recompute and the adjoint chain (by
+    // starting adjoint buffer)
+    cudaGraphExec_t g_rec[2] = {nullptr, nullptr};  // only [0] is used
     cudaGraphExec_t g_adj[2] = {nullptr, nullptr};
     cudaStream_t cap = nullptr;
 };
@@ -299,37 +347,30 @@ int tape_fail(tf_lbm_tape* tp, int code, const char* msg) { return handle_fail(t
         if (e_ != cudaSuccess) return handle_cuda_fail((tp)->H, e_, what);      \
     } while (0)
 
-// Recompute the len states of a segment from the state in buf[from]:
-// export, step, export, ..., export (len exports, len - 1 steps).
-cudaError_t recompute(tf_lbm_tape* tp, int from, int64_t len, cudaStream_t st)
+// Recompute the len states of a segment: seg slot 0 holds the checkpoint;
+// each step writes the next slot, so no state is exported or copied.
+cudaError_t recompute(tf_lbm_tape* tp, int64_t len, cudaStream_t st)
 {
-    tf_lbm_handle* H = tp->H;
-    const size_t sbytes = 9ull * H->G.nx * H->G.ny * H->esize;
     char* seg = (char*)tp->seg;
-    int cur = from;
-    for (int64_t i = 0; i < len; ++i) {
-        cudaError_t e = aux_export_state(H->desc, H->buf[cur], seg + i * sbytes, H->G, st);
-        if (e == cudaSuccess && i + 1 < len) {
-            e = launch_one_step(H, cur, st);
-            cur ^= 1;
-        }
+    for (int64_t i = 0; i + 1 < len; ++i) {
+        cudaError_t e = launch_step_between(tp->H, seg + i * tp->state_bytes, seg + (i + 1) * tp->state_bytes, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Adjoint steps backwards through a segment of len states, starting from the
-// adjoint state in abuf slot `from`.
+// Fused adjoint steps backwards through a segment of len states, starting
+// from the adjoint state in abuf slot `from`.
 cudaError_t adjoint_chain(tf_lbm_tape* tp, int from, int64_t len, cudaStream_t st)
 {
     tf_lbm_handle* H = tp->H;
-    const size_t sbytes = 9ull * H->G.nx * H->G.ny * H->esize;
+    const size_t abytes = 9ull * H->G.nx * H->G.ny * H->esize;
     char* seg = (char*)tp->seg;
     char* ab = (char*)tp->abuf;
     int cur = from;
     for (int64_t i = len - 1; i >= 0; --i) {
-        cudaError_t e = adjoint_step_dispatch(H, seg + i * sbytes, ab + cur * sbytes, ab + (cur ^ 1) * sbytes,
-                                              tp->gk, st);
+        cudaError_t e = adjoint_march_dispatch(H, seg + i * tp->state_bytes, ab + cur * abytes,
+                                               ab + (cur ^ 1) * abytes, tp->gk, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -395,9 +436,8 @@ int tf_lbm_tape_create(tf_lbm_handle* H, const void* h0, const void* theta, int6
         tf_lbm_tape_destroy(tp);
         return rc;
     };
-    if (!H->adj && (e = cudaMalloc(&H->adj, 10ull * n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc adjoint scratch");
     if ((e = cudaMalloc(&tp->ck, tp->state_bytes * (tp->nck + 1))) != cudaSuccess) return bail(e, "cudaMalloc checkpoints");
-    if ((e = cudaMalloc(&tp->seg, 9ull * n * H->esize * (every + 1))) != cudaSuccess) return bail(e, "cudaMalloc segment");
+    if ((e = cudaMalloc(&tp->seg, tp->state_bytes * every)) != cudaSuccess) return bail(e, "cudaMalloc segment");
     if ((e = cudaMalloc(&tp->abuf, 18ull * n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc adjoint");
     if ((e = cudaMalloc(&tp->gk, n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc grad kappa");
     if ((e = cudaMalloc(&tp->h0, n * H->esize)) != cudaSuccess) return bail(e, "cudaMalloc h0");
@@ -449,34 +489,28 @@ int tf_lbm_tape_backward(tf_lbm_tape* tp, const void* grad_h, void* grad_theta, 
     else k_seed<float><<<g1(D), 256, 0, st>>>((const float*)grad_h, (float*)ab, D);
     TK(tp, cudaGetLastError(), "seed kernel");
     TK(tp, cudaMemsetAsync(tp->gk, 0, n * H->esize, st), "cudaMemsetAsync");
-    const int saved_cur = H->cur;
     for (int c = tp->nck - 1; c >= 0; --c) {
         const int64_t len = (c + 1 == tp->nck) ? tp->nsteps - (int64_t)c * tp->every : tp->every;
-        // restore the checkpoint, recompute the segment's states, then run
+        // the checkpoint starts the segment; recompute its states, then run
         // the adjoint back through them; full segments replay captured graphs
-        TK(tp, cudaMemcpyAsync(H->buf[H->cur], ck + c * tp->state_bytes, tp->state_bytes, cudaMemcpyDeviceToDevice, st),
+        TK(tp, cudaMemcpyAsync(seg, ck + c * tp->state_bytes, tp->state_bytes, cudaMemcpyDeviceToDevice, st),
            "checkpoint restore");
         if (len == tp->every && len > 1) {
-            const int from = H->cur, afrom = cur;
-            if (!tp->g_rec[from])
-                TK(tp, capture(tp, &tp->g_rec[from], [&](cudaStream_t cs) { return recompute(tp, from, len, cs); }),
+            const int afrom = cur;
+            if (!tp->g_rec[0])
+                TK(tp, capture(tp, &tp->g_rec[0], [&](cudaStream_t cs) { return recompute(tp, len, cs); }),
                    "recompute graph");
             if (!tp->g_adj[afrom])
                 TK(tp, capture(tp, &tp->g_adj[afrom], [&](cudaStream_t cs) { return adjoint_chain(tp, afrom, len, cs); }),
                    "adjoint graph");
-            TK(tp, cudaGraphLaunch(tp->g_rec[from], st), "cudaGraphLaunch");
+            TK(tp, cudaGraphLaunch(tp->g_rec[0], st), "cudaGraphLaunch");
             TK(tp, cudaGraphLaunch(tp->g_adj[afrom], st), "cudaGraphLaunch");
         } else {
-            TK(tp, recompute(tp, H->cur, len, st), "recompute");
+            TK(tp, recompute(tp, len, st), "recompute");
             TK(tp, adjoint_chain(tp, cur, len, st), "adjoint chain");
         }
-        H->cur ^= (int)((len - 1) & 1);
         cur ^= (int)(len & 1);
     }
-    // the handle returns to the final state of the forward
-    H->cur = saved_cur;
-    TK(tp, cudaMemcpyAsync(H->buf[H->cur], ck + tp->nck * tp->state_bytes, tp->state_bytes, cudaMemcpyDeviceToDevice, st),
-       "final state restore");
     if (grad_h0 || grad_theta) {
         const double kc = (double)(H->p.n_exp - 1) * (H->p.m_exp - 1) / ((double)(H->p.n_exp - H->p.m_exp) * H->p.hstar);
         if (H->dbl)

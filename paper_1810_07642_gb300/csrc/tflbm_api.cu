@@ -189,6 +189,13 @@ cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
                        H->shape, st);
 }
 
+cudaError_t launch_step_between(tf_lbm_handle* H, const void* fin, void* fout, cudaStream_t st)
+{
+    const Consts<float> c32 = make_consts<float>(H);
+    const Consts<double> c64 = make_consts<double>(H);
+    return launch_step(H->desc.store, fin, fout, H->kappa, H->G, &c32, &c64, H->shape, st);
+}
+
 template Consts<float> make_consts<float>(const tf_lbm_handle*);
 template Consts<double> make_consts<double>(const tf_lbm_handle*);
 }  // namespace tflbm

@@ -48,6 +48,11 @@ template <typename T>
 Consts<T> make_consts(const tf_lbm_handle* H);
 // Launch one fused step from buf[from] into buf[from ^ 1].
 cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st);
+// Launch one fused step between two population buffers of the handle's layout.
+cudaError_t launch_step_between(tf_lbm_handle* H, const void* fin, void* fout, cudaStream_t st);
+// Fused adjoint step (tflbm_adjoint_march.cuh) from the raw buffer whose pull is f(t).
+cudaError_t adjoint_march_dispatch(tf_lbm_handle* H, const void* fin, const void* an, void* a, void* gk,
+                                   cudaStream_t st);
 // Record an error message on H (or for the calling thread when H is null).
 int handle_fail(tf_lbm_handle* H, int code, const std::string& msg);
 int handle_cuda_fail(tf_lbm_handle* H, cudaError_t e, const char* what);

@@ -147,3 +147,22 @@ def test_fp32_gradient_close_to_fp64():
     for k in range(2):
         a, b = grads["f32"][k], grads["f64"][k]
         assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_16bit_storage_gradient_close_to_fp64(dtype):
+    """With 16-bit population storage the tape differentiates the FP32 scheme
+    along the stored trajectory; its gradient stays within 2e-2 of the FP64
+    gradient (the trajectories themselves differ by the 16-bit rounding)."""
+    h0, th, tgt, p = inputs.inverse_design(64, seed=4)
+    T = 200
+    grads = {}
+    for dt in (dtype, "f64"):
+        theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+        hh = torch.tensor(h0, dtype=torch.float64, device="cuda")
+        tg = torch.tensor(tgt, device="cuda")
+        loss = 0.5 * ((evolve(theta, hh, p, T, dtype=dt).double() - tg) ** 2).sum()
+        loss.backward()
+        grads[dt] = theta.grad.cpu().numpy()
+    a, b = grads[dtype], grads["f64"]
+    assert np.abs(a - b).max() <= 2e-2 * np.abs(b).max()
