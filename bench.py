@@ -165,10 +165,45 @@ def oracle_cpu_baseline(budget_s: float = 15.0):
     t0 = time.perf_counter()
     O.step(cfg, kap, f, n)
     dt = time.perf_counter() - t0
-    return {"value": N_SIDE * N_SIDE * n / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": f"{n} full 2048x2048 steps of the FP64 oracle on the same inputs "
-                      f"({dt:.1f} s, {O.num_threads()} OpenMP threads)"}
+    out = {"value": N_SIDE * N_SIDE * n / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
+           "kind": "oracle",
+           "sample": f"{n} full 2048x2048 steps of the FP64 oracle on the same inputs "
+                     f"({dt:.1f} s, {O.num_threads()} OpenMP threads)"}
+    # the same oracle on one thread, over a 2048 x 64 band of the workload
+    threads = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        cfg.ny = 64
+        kb = O.kappa_field(cfg, th[:64])
+        fb = O.init(cfg, np.ascontiguousarray(h0[:64]))
+        t0 = time.perf_counter()
+        O.step(cfg, kb, fb, 1)
+        t1 = time.perf_counter() - t0
+        nb = int(max(2, min(200, 5.0 / max(t1, 1e-6))))
+        t0 = time.perf_counter()
+        O.step(cfg, kb, fb, nb)
+        dt1 = time.perf_counter() - t0
+        out["value_1_thread"] = N_SIDE * 64 * nb / dt1 / 1e6
+        out["sample_1_thread"] = f"{nb} steps of a 2048x64 periodic band ({dt1:.1f} s, 1 thread)"
+    finally:
+        O.set_num_threads(threads)
+    out["cpu"] = cpu_model()
+    return out
+
+
+def cpu_model() -> str:
+    """CPU model of the host, from /proc/cpuinfo where it names one."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as fh:
+            info = fh.read().splitlines()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info:
+                if line.startswith(key):
+                    return f"{platform.machine()}: {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def storage_variants(steps: int = 2000):

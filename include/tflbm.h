@@ -211,9 +211,9 @@ void tf_lbm_tape_destroy(tf_lbm_tape* tape);
  * Time candidate launch shapes of the fused step on the handle's own state
  * and keep the fastest.  Each candidate runs 2 untimed and `trial_steps`
  * timed steps (rounded up to even; <= 0 means 16), timed with CUDA events on
- * `stream`.  Candidates: block_x in {64, 128, 256}, both pipelines where the
- * bulk-copy one applies, and band heights around the one that fills a single
- * wave of resident CTAs.  The state is copied aside first (one population
+ * `stream`.  Candidates: block_x in {64, 128, 256}, every pipeline that
+ * applies, and band heights of one, two and three waves of resident CTAs and
+ * of 2 to 256 rows.  The state is copied aside first (one population
  * buffer of device memory, freed before return) and put back after, so f
  * and tf_lbm_time are as before the call.  The graph chunk is kept.
  * Synchronises `stream`.  best (host, may be NULL) receives the shape now in

@@ -255,14 +255,33 @@ __device__ __forceinline__ void block_store(Comp a, double* partials)
 
 // Sum of every stored population, decoded (the total liquid volume minus
 // nx*ny*href: streaming only permutes populations on the periodic lattice).
+// With an FP32 compute type each thread keeps an error-free FP32 pair
+// (sum, compensation; Knuth's TwoSum per element), which resolves the sum of
+// its ~100 values to about 2^-48 and runs at FP32 rate; the pair goes to the
+// double-precision block reduction once.  FP64 state sums in double.
 template <typename T, typename SM>
 __global__ void __launch_bounds__(kMassThreads) k_mass_partial(Pops<T, SM> P, Geom G, double* partials)
 {
     Comp a{0.0, 0.0};
+    float fs = 0.0f, fc = 0.0f;
     const long long nrows = 9LL * G.ny;
     for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
         const int l = (int)(row / G.ny), y = (int)(row % G.ny);
-        for (int x = threadIdx.x; x < G.nx; x += blockDim.x) comp_add(a, (double)P.raw(l, P.at(y, x)));
+        for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+            const T v = P.raw(l, P.at(y, x));
+            if constexpr (std::is_same<T, float>::value) {
+                const float t = __fadd_rn(fs, v);
+                const float bp = __fsub_rn(t, fs);
+                fc = __fadd_rn(fc, __fadd_rn(__fsub_rn(fs, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+                fs = t;
+            } else {
+                comp_add(a, (double)v);
+            }
+        }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        comp_add(a, (double)fs);
+        a.c += (double)fc;
     }
     block_store(a, partials);
 }

@@ -307,7 +307,7 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
                 const int bands = std::max(1, w * occ * sms / strips);
                 rows.push_back(std::max(16, (H->G.ny + bands - 1) / bands));
             }
-            for (int r : {32, 64, 128, 256}) rows.push_back(r);
+            for (int r : {2, 4, 8, 16, 32, 64, 128, 256}) rows.push_back(r);
             for (int r : rows) {
                 r = std::min(r, std::max(H->G.ny, 1));
                 Shape s;
@@ -607,7 +607,7 @@ int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch*
         const int occ = std::max(1, batch_occupancy(B, bx));
         std::vector<int> rows;
         for (int w = 1; w <= 3; ++w) rows.push_back(rows_for_slots(B, bx, (long long)w * occ * sms));
-        for (int r : {32, 64, 128, 256}) rows.push_back(std::min(r, ymax));
+        for (int r : {8, 16, 32, 64, 128, 256}) rows.push_back(std::min(r, ymax));
         for (int r : rows)
             for (int q : {0, 1}) {
                 bool dup = false;
