@@ -402,3 +402,42 @@ def test_no_slip_precursor_diverges_and_is_reported():
         if status:
             break
     assert status & (L.TF_LBM_STATUS_NONFINITE | L.TF_LBM_STATUS_NONPOSITIVE)
+
+
+def test_lattice_beyond_32bit_offsets_is_unsupported():
+    from paper_1810_07642_gb300.film import make_params
+    h0 = torch.ones(16, device="cuda")  # never read: the size check comes first
+    with pytest.raises(L.TfLbmError) as e:
+        L.tf_lbm_init(make_params(16384, 16384), h0.data_ptr(), None, 0)
+    assert e.value.code == L.TF_LBM_ERR_UNSUPPORTED and "2^31" in str(e.value)
+
+
+def test_largest_lattice_tiles_the_oracle():
+    """16000 x 14000 (9 ny pitch = 2.016e9 elements, just under the 2^31
+    offset limit; 16 GB of FP32 populations).  h0 is periodic with a 64 x 56
+    period that divides the lattice, so the solution is the tiling of the
+    solution on one 64 x 56 period: sampled nodes all over the lattice,
+    including the last rows and columns, must match the oracle run on that
+    period."""
+    nx, ny, px, py, steps = 16000, 14000, 64, 56, 10
+    hp, _, p = inputs.small_random(px, py, seed=21, amp=0.05)
+    p = dict(p, nx=nx, ny=ny, theta_uniform=math.radians(25.0), tau=0.9, gx_body=1e-5)
+    h0 = torch.as_tensor(hp, device="cuda").repeat(ny // py, nx // px)
+    sim = ThinFilm(p, h0, None, dtype="f32")
+    del h0
+    m0 = sim.mass()
+    sim.step(steps)
+    h = sim.h()
+    assert sim.check() == 0
+    assert abs(sim.mass() - m0) <= 1e-6 * m0
+    cfg = cfg_of(dict(p, nx=px, ny=py))
+    f = O.init(cfg, hp.astype(np.float32).astype(np.float64))
+    O.step(cfg, O.kappa_field(cfg, p["theta_uniform"]), f, steps)
+    ho = f.sum(0)
+    rng = np.random.default_rng(5)
+    ys = np.concatenate([rng.integers(0, ny, 200), [0, ny - 1, ny - 1]])
+    xs = np.concatenate([rng.integers(0, nx, 200), [nx - 1, 0, nx - 1]])
+    got = h[torch.as_tensor(ys, device="cuda"), torch.as_tensor(xs, device="cuda")].double().cpu().numpy()
+    want = ho[ys % py, xs % px]
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(ho).max()
+    sim.close()
