@@ -293,7 +293,7 @@ int march_rows(const tf_lbm_handle* H)
     }
     const int strips = (H->G.nx + BX - 9) / (BX - 8);
     const int bands = std::max(1, std::max(occ, 1) * sms / strips);
-    return std::max(8, (H->G.ny + bands - 1) / bands);
+    return std::max(4, (H->G.ny + bands - 1) / bands);
 }
 
 }  // namespace

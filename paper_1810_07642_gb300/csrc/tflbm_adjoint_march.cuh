@@ -4,22 +4,23 @@
 // Input: the raw population buffer whose pull is the state f(t) (exactly what
 // the forward step reads), a(t+1) = dL/df(t+1) and dL/dkappa so far; output
 // a(t) = dL/df(t), and dL/dkappa += the step's contribution.  Per node and
-// step: 36 B of populations, 36 B of a(t+1) (its second gather hits in
-// L1/L2), kappa, the read-modify-write of dL/dkappa and 36 B of a(t) in FP32.
+// step: 36 B of populations, 36 B of a(t+1) (gathered a second time, from
+// L1/L2, only when omega != 1), kappa, the read-modify-write of dL/dkappa and
+// 36 B of a(t) in FP32.
 //
 // A CTA of BX threads covers BX columns and marches down a band of rows like
 // the forward step.  The adjoint has four nested radius-1 stencils (h -> p ->
 // grad p and -h aF -> transposed gradient -> Laplacian), so CTAs overlap by
 // 8 columns and a band needs 4 halo rows on each side.  March step k, for
 // rows r(m) = rstart + m dir:
-//   A  row r(k):    pull f, h, j; gather mu_l = a_l(x + c_l, t+1); the
-//                   equilibrium and source adjoints at the node (aF, dL/dh
-//                   and dL/dj through f_eq)                 -> rings
+//   A  row r(k):    pull f, h, j                             -> rings
 //   (one __syncthreads)
 //   B  row r(k-1):  film pressure p (needs h of rows r(k-2) .. r(k))
-//   C  row r(k-3):  grad p (p rows r(k-4) .. r(k-2)); the force adjoint:
-//                   dL/dh += aF.(G - grad p) - fr'(h) aF.j, dL/dj -= fr aF,
-//                   ag = -h aF
+//   C  row r(k-3):  with mu_l = a_l(x + c_l, t+1) (loads issued before the
+//                   barrier), the equilibrium and source adjoints at the node (aF, dL/dh and dL/dj through
+//                   f_eq); grad p (p rows r(k-4) .. r(k-2)); the force
+//                   adjoint: dL/dh += aF.(G - grad p) - fr'(h) aF.j,
+//                   dL/dj -= fr aF, ag = -h aF
 //   D  row r(k-5):  transposed gradient of ag (rows r(k-6) .. r(k-4)):
 //                   ap; the disjoining-pressure adjoint into dL/dh and
 //                   dL/dkappa; alap = -gamma ap
@@ -36,7 +37,7 @@
 namespace tflbm {
 
 template <typename SM, typename T, int BX>
-__global__ void __launch_bounds__(BX)
+__global__ void __launch_bounds__(BX, sizeof(T) == 4 ? 768 / BX : 1)
 k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T* __restrict__ an,
                 T* __restrict__ a, T* __restrict__ gk, const T* __restrict__ kappa, const Geom G,
                 const Consts<T> C)
@@ -48,7 +49,7 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
     __shared__ T agx[4][BX], agy[4][BX];
     __shared__ T als[4][BX];   // -gamma ap
     // per-thread rings (own column)
-    __shared__ T rjx[4][BX], rjy[4][BX], rfx[4][BX], rfy[4][BX], rhe[4][BX], rjxe[4][BX], rjye[4][BX];
+    __shared__ T rjx[4][BX], rjy[4][BX];
     __shared__ T rah[8][BX], rajx[8][BX], rajy[8][BX];
 
     const int t = threadIdx.x;
@@ -71,6 +72,8 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
     // wrapped rows: r(k-1), r(k), r(k+1) (stages A, B); r(k-5) (D);
     // r(k-8), r(k-7), r(k-6) (E)
     int am = wrap_index(rstart - dir, ny), a0 = wrap_index(rstart, ny), ap1 = wrap_index(rstart + dir, ny);
+    int cm = wrap_index(rstart - 4 * dir, ny), c0 = wrap_index(rstart - 3 * dir, ny);
+    int cp = wrap_index(rstart - 2 * dir, ny);
     int d0 = wrap_index(rstart - 5 * dir, ny);
     int em = wrap_index(rstart - 8 * dir, ny), e0 = wrap_index(rstart - 7 * dir, ny);
     int ep = wrap_index(rstart - 6 * dir, ny);
@@ -108,29 +111,12 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
             hsm[k & 7][t] = dh;
             rjx[s4][t] = jx;
             rjy[s4][t] = jy;
-            T mu[9];
-            gather(y, yU, yD, mu);
-            // adjoints through the equilibria (Eq. equilibria, e = 1) and the
-            // source 3 w_l c_l . F, summed over l in closed form
-            const T h = dh + C.href, ih = fdiv(T(1), h);
-            const T ux = jx * ih, uy = jy * ih, q = ux * ux + uy * uy, gh = C.g * h;
-            const T p15 = mu[1] + mu[5], p37 = mu[3] + mu[7], p26 = mu[2] + mu[6], p48 = mu[4] + mu[8];
-            const T sax = p15 + p37, sdg = p26 + p48;
-            const T aFx = (mu[1] - mu[5]) * third + ((mu[2] - mu[6]) + (mu[8] - mu[4])) * twelfth;
-            const T aFy = (mu[3] - mu[7]) * third + ((mu[2] - mu[6]) + (mu[4] - mu[8])) * twelfth;
-            const T ua = ux + uy, ub = ux - uy;
-            const T ahe = mu[0] * (T(1) - T(5.0 / 3.0) * gh + T(2.0 / 3.0) * q)
-                        + (gh * third + q * T(1.0 / 6.0)) * sax - T(0.5) * (ux * ux * p15 + uy * uy * p37)
-                        + (gh * twelfth + q * T(1.0 / 24.0)) * sdg - T(0.125) * (ua * ua * p26 + ub * ub * p48);
-            const T cross_x = T(0.25) * (ua * p26 + ub * p48), cross_y = T(0.25) * (ua * p26 - ub * p48);
-            const T ajxe = -T(4.0 / 3.0) * ux * mu[0] + aFx + ux * p15 - ux * sax * third + cross_x - ux * sdg * twelfth;
-            const T ajye = -T(4.0 / 3.0) * uy * mu[0] + aFy + uy * p37 - uy * sax * third + cross_y - uy * sdg * twelfth;
-            rfx[s4][t] = aFx;
-            rfy[s4][t] = aFy;
-            rhe[s4][t] = C.omega * ahe;
-            rjxe[s4][t] = C.omega * ajxe;
-            rjye[s4][t] = C.omega * ajye;
         }
+        // mu_l = a_l(x + c_l, t+1) for stage C's row r(k-3), requested before
+        // the barrier so that the loads overlap it and stage B
+        T mu[9];
+        const bool runC = k >= 5 && k <= R + 8 && cC;
+        if (runC) gather(c0, dir > 0 ? cp : cm, dir > 0 ? cm : cp, mu);
         __syncthreads();
         // ---- B: film pressure of row r(k-1)
         if (k >= 2 && k <= R + 7 && cB) {
@@ -143,7 +129,7 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
             psm[m & 3][t] = film_pressure(hn, hc, hs, t, kap, ih, C, disj);
         }
         // ---- C: force adjoint at row r(k-3)
-        if (k >= 5 && k <= R + 8 && cC) {
+        if (runC) {
             const int m = k - 3, s4 = m & 3, s8 = m & 7;
             const T* pn = psm[(m + dir) & 3];
             const T* pc = psm[s4];
@@ -151,15 +137,30 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
             const T gpx = (pc[t + 1] - pc[t - 1]) * third + ((pn[t + 1] - pn[t - 1]) + (ps[t + 1] - ps[t - 1])) * twelfth;
             const T gpy = (pn[t] - ps[t]) * third + ((pn[t + 1] - ps[t + 1]) + (pn[t - 1] - ps[t - 1])) * twelfth;
             const T h = hsm[s8][t] + C.href;
-            const T Jx = rjx[s4][t], Jy = rjy[s4][t], aFx = rfx[s4][t], aFy = rfy[s4][t];
+            const T Jx = rjx[s4][t], Jy = rjy[s4][t];
+            // adjoints through the equilibria (Eq. equilibria, e = 1) and the
+            // source 3 w_l c_l . F, summed over l in closed form
+            const T ih = fdiv(T(1), h);
+            const T ux = Jx * ih, uy = Jy * ih, q = ux * ux + uy * uy, gh = C.g * h;
+            const T p15 = mu[1] + mu[5], p37 = mu[3] + mu[7], p26 = mu[2] + mu[6], p48 = mu[4] + mu[8];
+            const T sax = p15 + p37, sdg = p26 + p48;
+            const T aFx = (mu[1] - mu[5]) * third + ((mu[2] - mu[6]) + (mu[8] - mu[4])) * twelfth;
+            const T aFy = (mu[3] - mu[7]) * third + ((mu[2] - mu[6]) + (mu[4] - mu[8])) * twelfth;
+            const T ua = ux + uy, ub = ux - uy;
+            const T ahe = mu[0] * (T(1) - T(5.0 / 3.0) * gh + T(2.0 / 3.0) * q)
+                        + (gh * third + q * T(1.0 / 6.0)) * sax - T(0.5) * (ux * ux * p15 + uy * uy * p37)
+                        + (gh * twelfth + q * T(1.0 / 24.0)) * sdg - T(0.125) * (ua * ua * p26 + ub * ub * p48);
+            const T cross_x = T(0.25) * (ua * p26 + ub * p48), cross_y = T(0.25) * (ua * p26 - ub * p48);
+            const T ajxe = -T(4.0 / 3.0) * ux * mu[0] + aFx + ux * p15 - ux * sax * third + cross_x - ux * sdg * twelfth;
+            const T ajye = -T(4.0 / 3.0) * uy * mu[0] + aFy + uy * p37 - uy * sax * third + cross_y - uy * sdg * twelfth;
             // Eqs. (forcefric, alphafric): nu alpha u = fr j, fr = 6 nu / (2h^2 + 6 delta h + 3 delta^2)
             const T den = h * (T(2) * h + T(6) * C.delta) + T(3) * C.delta * C.delta;
             const T iden = fdiv(T(1), den);
             const T fr = C.nu6 * iden;
             const T dfr = -fr * (T(4) * h + T(6) * C.delta) * iden;
-            rah[s8][t] = rhe[s4][t] + aFx * (C.gx - gpx) + aFy * (C.gy - gpy) - dfr * (aFx * Jx + aFy * Jy);
-            rajx[s8][t] = rjxe[s4][t] - fr * aFx;
-            rajy[s8][t] = rjye[s4][t] - fr * aFy;
+            rah[s8][t] = C.omega * ahe + aFx * (C.gx - gpx) + aFy * (C.gy - gpy) - dfr * (aFx * Jx + aFy * Jy);
+            rajx[s8][t] = C.omega * ajxe - fr * aFx;
+            rajy[s8][t] = C.omega * ajye - fr * aFy;
             agx[s4][t] = -h * aFx;
             agy[s4][t] = -h * aFy;
         }
@@ -192,7 +193,12 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
             const T ajx = rajx[s8][t], ajy = rajy[s8][t], om = T(1) - C.omega;
             const int y = e0, yU = dir > 0 ? ep : em, yD = dir > 0 ? em : ep;
             T mu[9];
-            gather(y, yU, yD, mu);
+            if (om != T(0)) {
+                gather(y, yU, yD, mu);
+            } else {  // (1 - omega) mu_l vanishes at tau = 1
+#pragma unroll
+                for (int l = 0; l < 9; ++l) mu[l] = T(0);
+            }
             T* o = a + ((long long)y * nx + x);
             o[0] = ah + om * mu[0];
             o[n] = ah + ajx + om * mu[1];
@@ -207,6 +213,9 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
         adv(am);
         adv(a0);
         adv(ap1);
+        adv(cm);
+        adv(c0);
+        adv(cp);
         adv(d0);
         adv(em);
         adv(e0);
