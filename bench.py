@@ -698,15 +698,92 @@ def run_sweep(args):
     return 0
 
 
+def run_adjoint(args):
+    """--workload adjoint: gradients of the inverse-design loss as the timed
+    step (512^2, FP32, T = --adjoint-steps, sqrt(T) checkpoints): each step is
+    one checkpointed forward run plus the backward sweep of the hand-written
+    adjoint.  value = lattice updates of the forward horizon per second of
+    gradient (MLUPS-equivalent); the cost ratio against a plain forward run
+    of the same horizon is reported beside it."""
+    import torch
+    from paper_1810_07642_gb300 import build, inputs
+    from paper_1810_07642_gb300.adjoint import evolve
+    from paper_1810_07642_gb300.film import ThinFilm
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    n, T = 512, args.adjoint_steps
+    h0, th, tgt, p = inputs.inverse_design(n, seed=rank)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float32, device="cuda")
+    tg = torch.tensor(tgt, dtype=torch.float32, device="cuda")
+
+    def gradient(nsteps):
+        theta.grad = None
+        (0.5 * ((evolve(theta, hh, p, nsteps) - tg) ** 2).sum()).backward()
+
+    for _ in range(args.warmup):
+        gradient(300)
+    sim = ThinFilm(p, h0, th)
+    sim.step(100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(T)
+    sim.h()
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    sim.close()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            gradient(T)
+        torch.cuda.synchronize()
+        t_local = time.perf_counter() - t0
+    t_max = max_over_ranks(t_local, dist, "cuda")
+    every = int(math.ceil(math.sqrt(T)))
+    nck = (T + every - 1) // every
+    if rank == 0:
+        line = {"metric": METRIC, "value": aggregate_mlups(n * n, T * args.steps, world, t_max),
+                "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"inverse design gradient: {n}x{n} periodic, FP32, flat film "
+                                       f"with 1e-2 noise, theta 30 deg + 5 deg noise, 8-drop target, L2 "
+                                       f"loss, T={T}, checkpoints every {int(math.ceil(math.sqrt(T)))} "
+                                       f"steps", "l2": "L2-resident lattice (20 MB); timed on the host "
+                                       "clock around whole gradients"},
+                "adjoint_forward_cost_ratio": t_local / args.steps / t_fwd,
+                "forward_s": t_fwd,
+                # per gradient: T forward steps, T - nck recomputed steps, T adjoint
+                # steps, the seed, the initial-state adjoint and the final moments
+                "gpu_launches": args.steps * (3 * T - nck + 3), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="tflbm", choices=["tflbm", "reference"])
-    ap.add_argument("--workload", default="patterned", choices=["patterned", "sweep"],
+    ap.add_argument("--workload", default="patterned", choices=["patterned", "sweep", "adjoint"],
                     help="patterned: the 2048^2 dewetting run (default); sweep: the batched "
-                         "64-domain sliding-drop sweep as the timed step")
+                         "64-domain sliding-drop sweep as the timed step; adjoint: gradients of "
+                         "the 512^2 inverse-design loss")
+    ap.add_argument("--adjoint-steps", type=int, default=20000,
+                    help="adjoint workload: time steps of the forward horizon")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the patterned workload (arithmetic is FP32)")
     ap.add_argument("--batch-launch", default="",
@@ -720,6 +797,8 @@ def main():
         return run_reference(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_tflbm(args)
 
 
