@@ -7,6 +7,7 @@ synthetic stand-in).  Its populations (2 x 151 MB) and kappa field (17 MB)
 exceed the 129 MB L2, so no L2 flush is needed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {tflbm,reference}]
+                  [--workload {patterned,sweep,adjoint}] [--storage {f32,f16,bf16}]
 
 One step = one time step of the whole lattice = one launch of the fused
 kernel.  `value` is MLUPS = nodes x steps / time / 1e6 over all ranks (each
@@ -187,6 +188,25 @@ def oracle_cpu_baseline(budget_s: float = 15.0):
         out["sample_1_thread"] = f"{nb} steps of a 2048x64 periodic band ({dt1:.1f} s, 1 thread)"
     finally:
         O.set_num_threads(threads)
+    # smaller lattices of the paper's workloads (Rayleigh-Taylor 128^2, drop
+    # 512^2), all threads and one thread, short runs
+    by_size = {}
+    for label, mk, steps_all, steps_one in (
+            ("rayleigh_taylor_128", lambda: inputs.rayleigh_taylor(128, mode=1, g=-1e-4), 2000, 200),
+            ("sessile_drop_512", lambda: inputs.sessile_drop(512), 200, 10)):
+        hs, ths, ps = mk()
+        c = O.Config(**{k: v for k, v in ps.items() if k in O.Config.__dataclass_fields__})
+        ks = O.kappa_field(c, ths)
+        rec = {}
+        for nthr, nst in ((threads, steps_all), (1, steps_one)):
+            O.set_num_threads(nthr)
+            fs = O.init(c, hs)
+            t0 = time.perf_counter()
+            O.step(c, ks, fs, nst)
+            rec[f"mlups_{nthr}_threads"] = c.nx * c.ny * nst / (time.perf_counter() - t0) / 1e6
+        O.set_num_threads(threads)
+        by_size[label] = rec
+    out["by_size"] = by_size
     out["cpu"] = cpu_model()
     return out
 

@@ -31,7 +31,7 @@ struct tf_lbm_handle {
     int* status = nullptr;     // device word kernels set (kStatusTimeout)
     void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
     int64_t time = 0;
-    Shape shape{128, 64, kPipeTma};
+    Shape shape{128, 64, kPipeLdg};  // replaced by the occupancy-derived default in tf_lbm_init
     int graph_chunk = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
