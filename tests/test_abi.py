@@ -78,3 +78,16 @@ def test_oracle_and_library_share_no_code():
             text = open(os.path.join(ROOT, "oracle", fn)).read()
             assert not re.search(r"^\s*(import|from)\s+paper_1810_07642_gb300", text, re.M), fn
             assert not re.search(r"#\s*include\s+\S*tflbm", text), fn
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library absent every entry point
+    raises instead of computing anything elsewhere."""
+    from paper_1810_07642_gb300 import _lib as L
+    from paper_1810_07642_gb300 import build
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        L.tf_lbm_version()
+    with pytest.raises(RuntimeError, match="not built"):
+        L.tf_lbm_step(1, 1)

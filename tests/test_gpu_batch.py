@@ -206,7 +206,7 @@ def test_single_tuner_keeps_state_and_time(dtype):
     assert rel_linf(host_h(sim), oracle_h(h0, th, p, 100)) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
 def test_diagnostics_match_oracle_on_the_same_state(dtype):
     """Device diagnostics (single-handle and batched) against the oracle's
     plain definitions evaluated on the state the GPU exported."""
