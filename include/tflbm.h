@@ -298,6 +298,9 @@ typedef struct tf_lbm_batch_launch {
 int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32_t count, void* stream);
 /* Advance every handle of the batch by nsteps >= 0. */
 int tf_lbm_batch_step(tf_lbm_batch* B, int64_t nsteps, void* stream);
+/* Read or change the launch shape.  set_launch rewrites the work-item
+ * table in place, so it first waits for all work on the device
+ * (cudaDeviceSynchronize); ARG error on an invalid shape. */
 int tf_lbm_batch_get_launch(const tf_lbm_batch* B, tf_lbm_batch_launch* out);
 int tf_lbm_batch_set_launch(tf_lbm_batch* B, const tf_lbm_batch_launch* in);
 /* As tf_lbm_tune, over block_x, rows and queue, for the whole batch (every
