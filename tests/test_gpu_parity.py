@@ -441,3 +441,24 @@ def test_largest_lattice_tiles_the_oracle():
     want = ho[ys % py, xs % px]
     assert np.abs(got - want).max() <= 1e-5 * np.abs(ho).max()
     sim.close()
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_parity_random_configurations(case):
+    """Seeded random lattices (1..90 x 1..90) and parameters (tau, gamma, g,
+    delta, h*, (n, m), pi_sign, body force, theta field or uniform angle,
+    storage type), 60 steps, against the oracle."""
+    rng = np.random.default_rng(1000 + case)
+    nx, ny = int(rng.integers(1, 91)), int(rng.integers(1, 91))
+    dtype = ["f32", "f64", "f16", "bf16"][case % 4]
+    nm = [(3, 2), (9, 3), (4, 3)][int(rng.integers(0, 3))]
+    h0, th, p = inputs.small_random(nx, ny, seed=2000 + case, amp=float(rng.uniform(0.0, 0.1)))
+    p.update(tau=float(rng.uniform(0.6, 1.5)), gamma=float(rng.uniform(0.005, 0.02)),
+             g=float(rng.uniform(-5e-4, 5e-4)), delta=float(rng.uniform(0.5, 2.0)),
+             hstar=float(rng.uniform(0.05, 0.1)), n_exp=nm[0], m_exp=nm[1],
+             gx_body=float(rng.uniform(-1e-4, 1e-4)), gy_body=float(rng.uniform(-1e-4, 1e-4)))
+    uniform = bool(rng.integers(0, 2))
+    r = run_both(h0, th, p, 60, dtype, theta_uniform=float(np.radians(rng.uniform(5, 45))) if uniform else None)
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype], (nx, ny, dtype, p)
+    if dtype in ("f32", "f64"):
+        assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
