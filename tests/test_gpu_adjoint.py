@@ -166,3 +166,27 @@ def test_16bit_storage_gradient_close_to_fp64(dtype):
         grads[dt] = theta.grad.cpu().numpy()
     a, b = grads[dtype], grads["f64"]
     assert np.abs(a - b).max() <= 2e-2 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_tape_gradient_random_configurations(case):
+    """Seeded random lattices and parameters (tau, g, delta, (n, m), pi_sign,
+    body force), 25 steps with checkpoints every 4: the FP64 tape gradient
+    against the oracle's."""
+    rng = np.random.default_rng(3000 + case)
+    nx, ny = int(rng.integers(9, 48)), int(rng.integers(9, 48))
+    h0, th, p = inputs.small_random(nx, ny, seed=4000 + case, amp=0.08)
+    nm = [(3, 2), (9, 3), (4, 3)][case % 3]
+    p.update(tau=float(rng.uniform(0.6, 1.4)), g=float(rng.uniform(-5e-4, 5e-4)),
+             delta=float(rng.uniform(0.5, 2.0)), n_exp=nm[0], m_exp=nm[1],
+             pi_sign=1 if case < 5 else -1, gx_body=float(rng.uniform(-1e-4, 1e-4)))
+    T = 25
+    tgt = rng.uniform(0.9, 1.1, h0.shape)
+    L_o, gth_o, gh0_o, _ = _oracle_grads(p, h0, th, T, tgt)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = 0.5 * ((evolve(theta, hh, p, T, dtype="f64", every=4) - torch.tensor(tgt, device="cuda")) ** 2).sum()
+    loss.backward()
+    assert abs(loss.item() - L_o) <= 1e-11 * abs(L_o)
+    assert np.abs(theta.grad.cpu().numpy() - gth_o).max() <= 1e-9 * np.abs(gth_o).max()
+    assert np.abs(hh.grad.cpu().numpy() - gh0_o).max() <= 1e-9 * np.abs(gh0_o).max()
