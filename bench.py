@@ -476,6 +476,38 @@ def small_workloads():
     return out
 
 
+def term_balance(times=(1000, 5000, 20000)):
+    """The appendix's term balance (Eq. magnitude): L2 norms of the
+    x-components of the film-pressure term -h d_x p, the friction
+    -nu alpha(h) u_x and the longitudinal dissipation
+    nu lap(h u_x) + 2 nu d_x(div(h u)) over time, reduced on the device, for
+    a spreading drop (256^2, cap r_b = 60, h_d = 10, theta = 20 deg), a
+    sliding drop (256x128, Bo = 0.5) and a dewetting film (512^2 patterned),
+    FP32, tau = 1."""
+    from paper_1810_07642_gb300 import inputs
+    from paper_1810_07642_gb300.film import ThinFilm
+    cases = {}
+    h0, th, p = inputs.sessile_drop(256, rb=60.0, hd=10.0, theta_deg=20.0)
+    cases["spreading_drop_256"] = (h0, None, dict(p, theta_uniform=math.radians(20.0)))
+    (h0, th, p), = inputs.sliding_drops(count=1, bo_min=0.5, bo_max=0.5, lx_range=(256, 256), seed=2)
+    cases["sliding_drop_256x128"] = (h0, None, dict(p, theta_uniform=float(th[0, 0])))
+    h0, th, p = inputs.patterned_dewetting(512, seed=1)
+    cases["dewetting_512"] = (h0, th, p)
+    out = {}
+    for name, (h0, th, p) in cases.items():
+        sim = ThinFilm(p, h0, th)
+        t, rows = 0, []
+        for T in times:
+            sim.step(T - t)
+            t = T
+            tn = sim.term_norms().cpu().numpy()
+            rows.append({"t": T, "pressure": float(tn[0]), "friction": float(tn[1]),
+                         "dissipation": float(tn[2])})
+        out[name] = rows
+        sim.close()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step one oracle time step on a
     2048 x R periodic band of the workload, R sized to fit a few minutes."""
@@ -618,6 +650,7 @@ def run_tflbm(args):
         extras["adjoint"] = adjoint_cost()
         extras["batched_sweep"] = batched_sweep()
         extras["small_workloads"] = small_workloads()
+        extras["term_balance"] = term_balance()
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
