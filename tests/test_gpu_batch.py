@@ -197,7 +197,7 @@ def test_single_tuner_keeps_state_and_time(dtype):
     sim.step(5)
     before = sim.get_state().cpu().numpy()
     best = sim.tune(trial_steps=4)
-    assert best["block_x"] in (64, 128, 256) and best["pipeline"] in (0, 1)
+    assert best["block_x"] in (64, 128, 256) and best["pipeline"] in ((0, 1, 2) if dtype == "f32" else (0, 1))
     assert sim.launch == best
     assert np.array_equal(before, sim.get_state().cpu().numpy())
     assert sim.time == 5
