@@ -364,7 +364,12 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
 
     T v[9];
     T kap_n = C.kappa_u;
-    T fv[4][9];
+    // the pulled populations of the last four rows, needed by the relaxation
+    // when omega != 1: a per-thread shared ring in FP32 (keeps the kernel at
+    // 64 registers), registers in FP64
+    constexpr bool FRING = !OMEGA1 && sizeof(T) == 4;
+    __shared__ T fsm[FRING ? 4 : 1][9][FRING ? BX : 1];
+    T fv[FRING || OMEGA1 ? 1 : 4][9];
     T jxv[4], jyv[4], ihv[4], erv[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) { jxv[s] = jyv[s] = ihv[s] = erv[s] = T(0); }
@@ -429,7 +434,10 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
             hsm[s][t] = sum9(v, erv[s]);
             jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
             jyv[s] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
-            if (!OMEGA1) {
+            if constexpr (FRING) {
+#pragma unroll
+                for (int l = 0; l < 9; ++l) fsm[s][l][t] = v[l];
+            } else if constexpr (!OMEGA1) {
 #pragma unroll
                 for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
             }
@@ -446,8 +454,19 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
         // ---- (B2) force, collision and store of row r(k-3) (needs p rows r(k-4) .. r(k-2))
         if (B.ocol && k >= 5) {
             const int o = B.rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
+            T fl[9];
+            if constexpr (FRING) {
+#pragma unroll
+                for (int l = 0; l < 9; ++l) fl[l] = fsm[s3][l][t];
+            } else if constexpr (!OMEGA1) {
+#pragma unroll
+                for (int l = 0; l < 9; ++l) fl[l] = fv[s3][l];
+            } else {
+#pragma unroll
+                for (int l = 0; l < 9; ++l) fl[l] = T(0);  // unused at omega == 1
+            }
             collide_store<SM, T, OMEGA1>(dir > 0 ? psm[s2] : psm[s], psm[s3], dir > 0 ? psm[s] : psm[s2], t,
-                                         hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fv[s3],
+                                         hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fl,
                                          fout0, foutm, o * pitch, x, plane, C);
         }
         wm1 = w0;
@@ -477,7 +496,7 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
 }
 
 template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD, bool ASYNC = false>
-__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
+__global__ void __launch_bounds__(BX, sizeof(T) == 4 ? 1024 / BX : 1)
 k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
        SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
@@ -510,7 +529,7 @@ __device__ __forceinline__ void batch_item(const BatchItem it, const BatchDomain
 }
 
 template <typename SM, typename T, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1)
+__global__ void __launch_bounds__(BX, sizeof(T) == 4 ? 1024 / BX : 1)
 k_step_batch(const BatchItem* __restrict__ items, int nitems, const BatchDomain<T>* __restrict__ doms,
              int parity, int* queue)
 {
