@@ -575,6 +575,9 @@ def run_tflbm(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = ThinFilm(p, h0, th, dtype=args.storage, stream=stream)
+    if args.launch:
+        bx, rows, pipe = (int(v) for v in args.launch.split(","))
+        sim.set_launch(block_x=bx, rows=rows, pipeline=pipe)
     launch = sim.launch
     nodes = N_SIDE * N_SIDE
 
@@ -841,6 +844,9 @@ def main():
                     help="adjoint workload: time steps of the forward horizon")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the patterned workload (arithmetic is FP32)")
+    ap.add_argument("--launch", default="",
+                    help="patterned workload: block_x,rows,pipeline of the fused step instead of "
+                         "the library's default shape")
     ap.add_argument("--batch-launch", default="",
                     help="sweep workload: block_x,rows,graph_chunk,queue instead of autotuning")
     ap.add_argument("--skip-extras", action="store_true",

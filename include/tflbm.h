@@ -109,13 +109,21 @@ typedef struct tf_lbm_handle tf_lbm_handle;
  *   rows:    lattice rows marched by one CTA (>= 1);
  *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
  *            otherwise an even number >= 2);
- *   pipeline: 1 = every thread loads its own populations into registers,
- *            one row ahead (default); 2 = every thread copies its own
- *            populations into shared memory by asynchronous copies, two
- *            rows ahead (TF_LBM_F32 and TF_LBM_F64 only); 0 = row segments
- *            streamed into shared memory by bulk copies four rows ahead
- *            (needs nx a multiple of 8, >= 16).
- * Results do not depend on rows, graph_chunk or pipeline. */
+ *   pipeline: 3 = every thread owns two adjacent columns, loads aligned
+ *            pairs one row ahead, takes the values that cross a pair
+ *            boundary from the neighbouring lane and computes both nodes
+ *            with paired FP32 instructions (default when nx is even and the
+ *            dtype is not TF_LBM_F64); 4 = as 3, but the row segments are
+ *            staged in shared memory by bulk copies four rows ahead instead
+ *            of per-thread loads (nx a multiple of 8, >= 16, not
+ *            TF_LBM_F64); 1 = every thread loads its own column
+ *            into registers, one row ahead (default otherwise); 2 = every
+ *            thread copies its own populations into shared memory by
+ *            asynchronous copies, two rows ahead (TF_LBM_F32 and TF_LBM_F64
+ *            only); 0 = row segments streamed into shared memory by bulk
+ *            copies four rows ahead (needs nx a multiple of 8, >= 16).
+ * Results do not depend on rows or graph_chunk; the pipelines agree to
+ * rounding. */
 typedef struct tf_lbm_launch {
     int32_t block_x;
     int32_t rows;
@@ -174,6 +182,16 @@ int64_t tf_lbm_time(const tf_lbm_handle* H);
 /* Read or change the launch shape (see tf_lbm_launch). */
 int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out);
 int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in);
+
+/* How long a bulk-copy step kernel (pipelines 0 and 4) waits for one of its
+ * own row copies before giving up: `polls` tests of the copy's completion
+ * barrier (polls < 0 restores the default, 2^22; polls == 0 gives up at
+ * once).  A kernel that gives up sets TF_LBM_STATUS_TIMEOUT (tf_lbm_check),
+ * stops issuing copies, waits (with the default bound) for the copies it has
+ * already issued and returns; the populations of that step are invalid.
+ * This exists to exercise that path without a fault: no paper counterpart.
+ * Later steps of the same handle keep TF_LBM_STATUS_TIMEOUT set. */
+int tf_lbm_set_wait_limit(tf_lbm_handle* H, int32_t polls);
 
 /* ---------------------------------------------------------------- adjoint
  * Reverse-mode derivative of the step (not in the paper; the method's own
@@ -330,9 +348,12 @@ const char* tf_lbm_batch_last_error(const tf_lbm_batch* B);
  * loops that cannot afford cudaMalloc's possible device-wide synchronisation.
  * Summing the state exported by tf_lbm_get_state gives the total volume that
  * tf_lbm_mass reports, without a handle-side allocation.
- *   x:   device (or managed) array of n doubles; may be NULL when n == 0.
+ *   x:   device (or managed) array of n doubles on the current device; may
+ *        be NULL when n == 0.
  *   n:   0 <= n <= TF_LBM_NOALLOC_MAX_ELEMS, else TF_LBM_ERR_ARG.
- *   out: device (or managed) double; written asynchronously on `stream`.
+ *   out: device (or managed) double on the current device; written
+ *        asynchronously on `stream`.
+ * Host pointers and device memory of another GPU are TF_LBM_ERR_ARG.
  * Block partial sums go to a fixed 64 KB file-scope device array that every
  * GPU loading the library keeps until exit.  Its device address is looked up
  * on the first call made on each device, so make that first call before any

@@ -25,7 +25,7 @@ EXPORTED = [
     "tf_lbm_tape_backward", "tf_lbm_tape_destroy", "tf_lbm_tune", "tf_lbm_diagnostics",
     "tf_lbm_batch_create", "tf_lbm_batch_step", "tf_lbm_batch_get_launch", "tf_lbm_batch_set_launch",
     "tf_lbm_batch_tune", "tf_lbm_batch_diagnostics", "tf_lbm_batch_items", "tf_lbm_batch_destroy",
-    "tf_lbm_batch_last_error", "tf_lbm_term_norms",
+    "tf_lbm_batch_last_error", "tf_lbm_term_norms", "tf_lbm_set_wait_limit",
 ]
 # fields of tf_lbm_diag, in order
 DIAG_FIELDS = ("mass", "wet_mass", "wet_jx", "wet_jy", "wet_area", "h_max",
@@ -93,6 +93,7 @@ def lib():
     L.tf_lbm_time.restype = i64
     L.tf_lbm_get_launch.argtypes = [_VP, ctypes.POINTER(Launch)]
     L.tf_lbm_set_launch.argtypes = [_VP, ctypes.POINTER(Launch)]
+    L.tf_lbm_set_wait_limit.argtypes = [_VP, i32]
     L.tf_lbm_destroy.argtypes = [_VP]
     L.tf_lbm_destroy.restype = None
     L.tf_lbm_last_error.argtypes = [_VP]
@@ -189,6 +190,10 @@ def tf_lbm_set_launch(handle: int, block_x: int, rows: int, graph_chunk: int,
                       pipeline: int = 0) -> None:
     L = Launch(block_x, rows, graph_chunk, pipeline)
     _check(lib().tf_lbm_set_launch(_VP(handle), ctypes.byref(L)), _VP(handle))
+
+
+def tf_lbm_set_wait_limit(handle: int, polls: int) -> None:
+    _check(lib().tf_lbm_set_wait_limit(_VP(handle), int(polls)), _VP(handle))
 
 
 def tf_lbm_destroy(handle: int) -> None:

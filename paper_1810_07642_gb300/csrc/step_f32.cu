@@ -1,6 +1,7 @@
-// FP32 and FP64 instantiations of the fused step (tflbm_step.cuh) and the
-// dispatch over storage types.
-#include "tflbm_step.cuh"
+// FP32 and FP64 instantiations of the fused step (tflbm_step.cuh, and the
+// paired-column kernel of tflbm_step2.cuh for FP32) and the dispatch over
+// storage types.
+#include "tflbm_step2.cuh"
 
 namespace tflbm {
 
@@ -19,6 +20,9 @@ static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, 
     T* g0 = (T*)fout;
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
     const T* k = (const T*)kappa;
+    if constexpr (std::is_same<T, float>::value)
+        if (is_pair_pipeline(S.pipeline))
+            return launch_pair<SM>(S.pipeline == kPipePairTma, S.block_x, f0, fm, g0, gm, k, G, C, S.rows, st);
     switch (S.block_x) {
         case 64: return launch_step_bx<SM, T, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
         case 128: return launch_step_bx<SM, T, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
@@ -40,6 +44,8 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
 
 int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield)
 {
+    if (store == kStoreF32 && is_pair_pipeline(pipeline))
+        return blocks_per_sm_pair<float>(pipeline == kPipePairTma, block_x, omega1, kfield);
     if (store == kStoreF32 || store == kStoreF64) {
         const bool f = store == kStoreF32;
         switch (block_x) {

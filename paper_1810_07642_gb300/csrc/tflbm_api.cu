@@ -95,10 +95,6 @@ int validate(const tf_lbm_params* p)
     return TF_LBM_OK;
 }
 
-// Default launch shape: 128-wide CTAs on wide lattices, 64 otherwise, and a
-// band height that makes the grid one full wave of resident CTAs (all bands
-// do the same work, so a partial second wave would idle most SMs), but no
-// shorter than 16 rows: each band spends 5 warm-up rows.
 int store_of(int dtype)
 {
     switch (dtype) {
@@ -109,20 +105,30 @@ int store_of(int dtype)
     }
 }
 
+// Default launch shape: the two-column kernel where it applies, CTAs 256
+// columns wide on wide lattices (128 for the one-column kernels) and half
+// that otherwise, and a band height that makes the grid one full wave of
+// resident CTAs (all bands do the same work, so a partial second wave would
+// idle most SMs), but no shorter than 16 rows: each band spends 5 warm-up rows.
 Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 {
     Shape s;
-    s.block_x = G.nx >= 1024 ? 128 : 64;
+    // two columns per thread where pairs fit (nx even) for 16-bit storage:
+    // it issues fewer instructions per node than the one-column kernel, whose
+    // decode and encode work makes it issue bound; FP32 storage keeps the
+    // one-column kernel, which measured faster
+    const int store = store_of(p.dtype);
+    const bool pair = pair_pipeline_ok(G.nx, store) && (store == kStoreF16 || store == kStoreBF16);
+    s.block_x = pair ? (G.nx >= 1024 ? 256 : 128) : (G.nx >= 1024 ? 128 : 64);
     const int strips = (G.nx + s.block_x - 5) / (s.block_x - 4);  // CTAs overlap by 4 columns
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool om1 = p.tau == 1.0;
-    // per-thread loads: measured faster than the bulk-copy pipeline on GB300
-    // for this kernel, which is instruction-issue bound rather than latency
-    // bound once loads are prefetched a row ahead
-    s.pipeline = kPipeLdg;
+    // otherwise per-thread loads: measured faster than the bulk-copy pipeline
+    // on GB300 once loads are prefetched a row ahead
+    s.pipeline = pair ? kPipePair : kPipeLdg;
     int occ = step_blocks_per_sm(store_of(p.dtype), s.pipeline, s.block_x, om1, kfield);
     if (occ < 1) occ = 4;
     int bands = occ * sms / strips;
@@ -178,6 +184,7 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
     C.status = H->status;
+    C.wait_limit = H->wait_limit;
     return C;
 }
 
@@ -443,9 +450,16 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     if (in->rows < 1 || in->rows > 65535) return fail(H, TF_LBM_ERR_ARG, "rows must be in [1, 65535]");
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
-    if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg && in->pipeline != kPipeAsync)
+    if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg && in->pipeline != kPipeAsync &&
+        in->pipeline != kPipePair && in->pipeline != kPipePairTma)
         return fail(H, TF_LBM_ERR_ARG,
-                    "pipeline must be 0 (bulk copies), 1 (per-thread loads) or 2 (per-thread async copies)");
+                    "pipeline must be 0 (bulk copies), 1 (per-thread loads), 2 (per-thread async copies), "
+                    "3 (two columns per thread) or 4 (two columns per thread, bulk copies)");
+    if (in->pipeline == kPipePair && !pair_pipeline_ok(H->G.nx, H->desc.store))
+        return fail(H, TF_LBM_ERR_ARG, "the two-column pipeline needs nx even and an FP32 compute type");
+    if (in->pipeline == kPipePairTma && !pair_tma_pipeline_ok(H->G.nx, H->desc.store))
+        return fail(H, TF_LBM_ERR_ARG,
+                    "the two-column bulk-copy pipeline needs nx a multiple of 8, >= 16, and an FP32 compute type");
     if (in->pipeline == kPipeAsync && H->msize != H->esize)
         return fail(H, TF_LBM_ERR_ARG, "the async-copy pipeline needs FP32 or FP64 storage");
     if (in->pipeline == kPipeTma && !tma_pipeline_ok(H->G.nx))
@@ -455,6 +469,14 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     H->shape.block_x = bx;
     H->shape.rows = in->rows;
     H->graph_chunk = in->graph_chunk;
+    return TF_LBM_OK;
+}
+
+int tf_lbm_set_wait_limit(tf_lbm_handle* H, int32_t polls)
+{
+    if (!H) return fail(nullptr, TF_LBM_ERR_ARG, "handle is NULL");
+    H->wait_limit = polls < 0 ? kWaitLimit : polls;
+    drop_graphs(H);  // captured launches carry the old limit
     return TF_LBM_OK;
 }
 

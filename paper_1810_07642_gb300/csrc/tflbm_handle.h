@@ -29,6 +29,7 @@ struct tf_lbm_handle {
     int nmass = 0;
     int* flag = nullptr;
     int* status = nullptr;     // device word kernels set (kStatusTimeout)
+    int wait_limit = kWaitLimit;  // polls of one mbarrier before a bulk-copy kernel gives up
     void* diag = nullptr;      // 2 * ny * nx scratch for tf_lbm_pressure_force (lazy)
     int64_t time = 0;
     Shape shape{128, 64, kPipeLdg};  // replaced by the occupancy-derived default in tf_lbm_init

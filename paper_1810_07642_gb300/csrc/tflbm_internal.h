@@ -18,10 +18,18 @@ struct Geom {
 constexpr int kPipeTma = 0;
 constexpr int kPipeLdg = 1;
 constexpr int kPipeAsync = 2;  // per-thread cp.async staging (full-width storage only)
+constexpr int kPipePair = 3;     // two columns per thread, per-thread loads (FP32 compute type, nx even)
+constexpr int kPipePairTma = 4;  // two columns per thread, rows staged by bulk copies (also nx % 8 == 0)
 inline bool tma_pipeline_ok(int nx) { return nx % 8 == 0 && nx >= 16; }
+inline bool pair_pipeline_ok(int nx, int store) { return nx % 2 == 0 && store != 1 /* kStoreF64 */; }
+inline bool pair_tma_pipeline_ok(int nx, int store) { return pair_pipeline_ok(nx, store) && tma_pipeline_ok(nx); }
+inline bool is_pair_pipeline(int pipeline) { return pipeline == kPipePair || pipeline == kPipePairTma; }
 
 // Status bit a kernel sets when an mbarrier wait gave up (tf_lbm_check).
 constexpr int kStatusTimeout = 4;
+// Polls of one mbarrier before a bulk-copy kernel gives up (the default of
+// Consts::wait_limit).
+constexpr int kWaitLimit = 1 << 22;
 
 // Per-run constants of the step, in the compute type T.
 template <typename T>
@@ -41,7 +49,8 @@ struct Consts {
     T mscale, minv, r_axis, r_diag;
     T nr_axis, nr_diag;  // -r_axis * mscale, -r_diag * mscale (exact: mscale is a power of 2)
     int n_exp, m_exp;
-    int* status;  // device word for kStatusTimeout (may be null)
+    int* status;     // device word for kStatusTimeout (may be null)
+    int wait_limit;  // polls of one mbarrier before giving up (<= 0: give up at once)
 };
 
 // Launch shape of the fused step.

@@ -154,6 +154,19 @@ int device_pointer(const void* p, const char* name)
         tflbm::set_thread_error(std::string(name) + " must be device or managed memory");
         return TF_LBM_ERR_ARG;
     }
+    // memory of another GPU would be read (or written) from this one, which
+    // without peer access is an illegal address, not an argument error
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        tflbm::set_thread_error("cudaGetDevice failed");
+        return TF_LBM_ERR_CUDA;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        tflbm::set_thread_error(std::string(name) + " lives on device " + std::to_string(a.device) +
+                                ", not on the current device " + std::to_string(dev));
+        return TF_LBM_ERR_ARG;
+    }
     return TF_LBM_OK;
 }
 

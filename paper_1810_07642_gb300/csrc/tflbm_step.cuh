@@ -600,8 +600,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-constexpr int kStages = 4;           // TMA pipeline depth, in march steps
-constexpr int kWaitLimit = 1 << 22;  // polls of one mbarrier before giving up
+constexpr int kStages = 4;  // TMA pipeline depth, in march steps
 
 // Shared-memory layout of one pipeline stage: plane 0 (compute type) then the
 // 8 moving planes (storage type), LMAX elements each.  LMAX covers the
@@ -691,7 +690,7 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
         issue_step<SM, T>(stage_mem + st * L::STAGE, &bars[st], fin0, finm, plane, pitch, nx, ny,
                           wrap_index(B.rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step);
     };
-    bool timed_out = false;
+    bool gave_up = false;  // this thread stopped waiting for a stage
 
     if (t == 0) {
 #pragma unroll
@@ -710,23 +709,28 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
 #pragma unroll
     for (int s = 0; s < 4; ++s) { jxv[s] = jyv[s] = ihv[s] = erv[s] = T(0); }
 
-    auto body = [&](auto stage_c, int k) {
+    // one march step; false when the CTA gave up waiting for a bulk copy
+    auto body = [&](auto stage_c, int k) -> bool {
         constexpr int s = decltype(stage_c)::value;  // ring slot and pipeline stage of row r(k)
         constexpr int s1 = (s + 3) & 3;              // slot of row r(k-1)
         constexpr int s2 = (s + 2) & 3;              // slot of row r(k-2)
         constexpr int s3 = (s + 1) & 3;              // slot of row r(k-3)
         const T kap = kap_n;                         // kappa of row r(k-1)
         // ---- (A) h of row r(k) from the stage that holds its pulled rows
-        if (k <= R + 3) {
+        if (k <= R + 3 && B.hcol) {
             const uint32_t parity = (uint32_t)(k / kStages) & 1u;
-            int it = 0;
-            while (!mbar_test(&bars[s], parity)) {
-                if (++it >= kWaitLimit) {
-                    timed_out = true;
-                    break;
+            if (C.wait_limit <= 0) {
+                gave_up = true;
+            } else {
+                int it = 0;
+                while (!mbar_test(&bars[s], parity)) {
+                    if (++it >= C.wait_limit) {
+                        gave_up = true;
+                        break;
+                    }
                 }
             }
-            if (B.hcol) {
+            if (!gave_up) {
                 const unsigned char* base = stage_mem + s * L::STAGE;
                 const T* p0 = reinterpret_cast<const T*>(base);
                 const SM* pm = reinterpret_cast<const SM*>(base + L::B0);
@@ -752,8 +756,9 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
                 if (KFIELD && B.pcol) kap_n = kappa[(long long)wk * nx + x];  // row r(k), used next step
             }
         }
-        __syncthreads();
-        // every thread is done with this stage: refill it for step k + kStages
+        // every thread is done with this stage (or the CTA gives up): refill
+        // it for step k + kStages
+        if (__syncthreads_or(gave_up)) return false;
         if (t < 32 && k + kStages <= R + 3) issue(k + kStages);
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
         if (B.pcol && k >= 2 && k <= R + 3) {
@@ -770,32 +775,36 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
         }
         wk += dir;
         wk = wk == ny ? 0 : (wk < 0 ? ny - 1 : wk);
+        return true;
     };
 
     const int last = R + 4;
-    for (int k = 0;;) {
-        body(std::integral_constant<int, 0>{}, k);
+    int k = 0;
+    bool ok = true;
+    for (;;) {
+        if (!(ok = body(std::integral_constant<int, 0>{}, k))) break;
         if (++k > last) break;
-        body(std::integral_constant<int, 1>{}, k);
+        if (!(ok = body(std::integral_constant<int, 1>{}, k))) break;
         if (++k > last) break;
-        body(std::integral_constant<int, 2>{}, k);
+        if (!(ok = body(std::integral_constant<int, 2>{}, k))) break;
         if (++k > last) break;
-        body(std::integral_constant<int, 3>{}, k);
+        if (!(ok = body(std::integral_constant<int, 3>{}, k))) break;
         if (++k > last) break;
     }
 
-    if (timed_out) {
-        // report, then give the copies still in flight a bounded chance to
-        // land before the CTA's shared memory is released
+    if (!ok && t == 0) {
+        // report, then wait (bounded) for the copies still in flight before
+        // the CTA's shared memory is released.  The CTA stopped at step k
+        // before issuing step k + kStages, so the last step issued is jmax;
+        // no stage is refilled before all threads passed its previous phase,
+        // so each stage has at most one unfinished phase: its last issued step.
         if (C.status) atomicOr(C.status, kStatusTimeout);
-        if (t == 0) {
-            for (int s = 0; s < kStages; ++s) {
-                const int jl = (R + 3) - ((((R + 3) - s) % kStages + kStages) % kStages);
-                if (jl >= 0) {
-                    int it = 0;
-                    while (!mbar_test(&bars[s], (uint32_t)(jl / kStages) & 1u) && ++it < kWaitLimit) {
-                    }
-                }
+        const int jmax = min(k + kStages - 1, R + 3);
+        for (int s = 0; s < kStages; ++s) {
+            if (jmax < s) continue;
+            const int jl = jmax - ((jmax - s) % kStages);
+            int it = 0;
+            while (!mbar_test(&bars[s], (uint32_t)(jl / kStages) & 1u) && ++it < kWaitLimit) {
             }
         }
     }

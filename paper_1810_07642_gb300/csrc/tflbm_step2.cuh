@@ -1,0 +1,707 @@
+// Paired-column fused step: the same time step as step_band (Section II of
+// Zitz et al., arXiv:1810.07642: Eqs. LBE, equilibria, force, pfilm,
+// disjoiningP, forcefric, alphafric, derivative, n_laplace), arranged so that
+// each thread owns two adjacent lattice columns.
+//
+// Why: the one-column kernel issues about ten warp instructions per node and
+// is limited by instruction issue, not by HBM.  Two columns per thread halve
+// the per-node cost of addressing, loop control, shared-memory traffic and
+// barriers, turn every population load and store into one aligned 8-byte
+// (FP32) or 4-byte (16-bit pair) access, and let the node arithmetic run on
+// Blackwell's paired FP32 instructions (two lanes of float math per issued
+// instruction).
+//
+// Streaming without misaligned loads.  Thread t loads the nine planes at its
+// own aligned column pair (c, c+1).  Populations with c_x = 0 arrive from the
+// same columns.  Those with c_x = +1 (l = 1, 2, 8) arrive from the column to
+// the left and those with c_x = -1 (l = 4, 5, 6) from the right, so only one
+// value per direction crosses a pair boundary; it comes from the neighbouring
+// lane by a warp shuffle.  At tau = 1 only their sums matter (the collision
+// needs h and j alone), so per row four shuffles move the partial sums
+// R = f1 + f2 + f8, L = f4 + f5 + f6 and their y-momenta.  Lane 0 and lane 31
+// of every warp read the three planes of their outer neighbour column
+// themselves (predicated loads that hit L1/L2).
+//
+// Rows, bands, shared rings, the reference-height storage and the exact mass
+// folding are those of step_band (tflbm_step.cuh).  Needs nx even (pairs
+// never straddle the periodic seam); compute type FP32, storage FP32, FP16 or
+// BF16.
+#pragma once
+#include "tflbm_step.cuh"
+
+namespace tflbm {
+
+// ---- paired FP32 arithmetic (one instruction for both columns) ------------
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Error-free TwoSum on both lanes: a + b = s + e exactly.
+__device__ __forceinline__ void ptwo_sum(float2 a, float2 b, float2& s, float2& e)
+{
+    s = padd(a, b);
+    const float2 bb = psub(s, a);
+    e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+
+// ---- pair storage of the moving populations --------------------------------
+// V is one aligned pair of stored values; dec gives the two stored values as
+// floats, enc rounds two floats to the storage type.
+template <typename SM> struct PairIO;
+template <> struct PairIO<float> {
+    using V = float2;
+    static __device__ __forceinline__ float2 dec(float2 q) { return q; }
+    static __device__ __forceinline__ float2 enc(float2 v) { return v; }
+};
+template <> struct PairIO<__half> {
+    using V = __half2;
+    static __device__ __forceinline__ float2 dec(__half2 q) { return __half22float2(q); }
+    static __device__ __forceinline__ __half2 enc(float2 v) { return __float22half2_rn(v); }
+};
+template <> struct PairIO<__nv_bfloat16> {
+    using V = __nv_bfloat162;
+    static __device__ __forceinline__ float2 dec(__nv_bfloat162 q) { return __bfloat1622float2(q); }
+    static __device__ __forceinline__ __nv_bfloat162 enc(float2 v) { return __float22bfloat162_rn(v); }
+};
+
+template <typename V> __device__ __forceinline__ V ldpair(const V* p) { return __ldg(p); }
+template <typename V> __device__ __forceinline__ uint32_t bits(V v)
+{
+    static_assert(sizeof(V) == 4, "16-bit pairs only");
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+template <typename V> __device__ __forceinline__ V from_bits(uint32_t u)
+{
+    V v;
+    memcpy(&v, &u, 4);
+    return v;
+}
+
+// Stored pair -> population values (16-bit: q / scale + R_l, one fma each).
+template <typename SM>
+__device__ __forceinline__ float2 decode_pair(typename PairIO<SM>::V q, float R, const Consts<float>& C)
+{
+    if constexpr (std::is_same<SM, float>::value) return q;
+    else return pfma(PairIO<SM>::dec(q), pk(C.minv), pk(R));
+}
+
+// Population values -> stored pair, and o replaced by what readers decode.
+template <typename SM>
+__device__ __forceinline__ typename PairIO<SM>::V narrow_pair(float2& o, float R, float NR, const Consts<float>& C)
+{
+    const typename PairIO<SM>::V q = PairIO<SM>::enc(pfma(o, pk(C.mscale), pk(NR)));
+    o = pfma(PairIO<SM>::dec(q), pk(C.minv), pk(R));
+    return q;
+}
+
+
+// ---------------------------------------------------------------------------
+// Node arithmetic shared by both load paths.
+
+// h - href, its pull-sum residual and j of the two nodes from their pulled
+// populations n[l-1] (l = 1..8) and f_0 - href.  The moving populations are
+// summed first (they are small), the last addition is error-free (see sum9).
+__device__ __forceinline__ void pair_moments(const float2 (&n)[8], float2 f0, float2& dh, float2& er,
+                                             float2& jx, float2& jy)
+{
+    const float2 rs = padd(padd(n[0], n[1]), n[7]);  // c_x = +1: l = 1, 2, 8
+    const float2 ls = padd(padd(n[4], n[3]), n[5]);  // c_x = -1: l = 5, 4, 6
+    ptwo_sum(f0, padd(padd(padd(n[2], n[6]), rs), ls), dh, er);
+    jx = psub(rs, ls);
+    jy = padd(padd(psub(n[2], n[6]), psub(n[1], n[7])), psub(n[3], n[5]));
+}
+
+// Film pressure (Eq. pfilm with Eq. disjoiningP) of the two nodes from the
+// shared h rows n (+y), c, s (-y) at the pair's slot; writes 1/h to ih.
+__device__ __forceinline__ float2 pair_pressure(const float* hn, const float* hc, const float* hs, float2 kap,
+                                                bool disj, const Consts<float>& C, float2& ih)
+{
+    const float2 c0 = *reinterpret_cast<const float2*>(hc);
+    const float2 n0 = *reinterpret_cast<const float2*>(hn);
+    const float2 s0 = *reinterpret_cast<const float2*>(hs);
+    const float cl = hc[-1], cr = hc[2], nl = hn[-1], nr = hn[2], sl = hs[-1], sr = hs[2];
+    // Eq. (n_laplace): axis neighbours left + right + up + down, diagonal the four corners
+    const float2 axis = padd(padd(make_float2(cl, c0.x), make_float2(c0.y, cr)), padd(n0, s0));
+    const float2 diag = padd(padd(make_float2(nl, n0.x), make_float2(n0.y, nr)),
+                             padd(make_float2(sl, s0.x), make_float2(s0.y, sr)));
+    float2 lap = pmul(pfma(pk(4.0f), axis, pfma(pk(-20.0f), c0, diag)), pk(1.0f / 6.0f));
+    const float2 h = padd(c0, pk(C.href));
+    ih = make_float2(__fdividef(1.0f, h.x), __fdividef(1.0f, h.y));
+    if (disj) {
+        const float2 r = pmul(pk(C.hstar), ih);
+        float2 fd;
+        if (C.n_exp == 3 && C.m_exp == 2) fd = pmul(pmul(r, r), psub(r, pk(1.0f)));
+        else fd = make_float2(fdisj(r.x, C.n_exp, C.m_exp), fdisj(r.y, C.n_exp, C.m_exp));
+        lap = pfma(pmul(pk(C.pi_sgn), kap), fd, lap);
+    }
+    return pmul(pk(-C.gamma), lap);
+}
+
+// Force, collision and store of the two nodes (the arithmetic of
+// collide_store on both lanes).  pn, pc, ps: shared p rows o+1, o, o-1 at the
+// pair's slot; f: the pulled moving populations (omega != 1 only); i: the
+// storage offset of the pair's first column.
+template <typename SM, bool OMEGA1>
+__device__ __forceinline__ void pair_collide_store(const float* pn, const float* pc, const float* ps, float2 dh,
+                                                   float2 ih, float2 jx, float2 jy, float2 er,
+                                                   const float2* f, int fstride, float* __restrict__ fout0,
+                                                   SM* __restrict__ foutm, int i, int plane,
+                                                   const Consts<float>& C)
+{
+    using V = typename PairIO<SM>::V;
+    constexpr bool NARROW = !std::is_same<SM, float>::value;
+    const float2 n0 = *reinterpret_cast<const float2*>(pn);
+    const float2 c0 = *reinterpret_cast<const float2*>(pc);
+    const float2 s0 = *reinterpret_cast<const float2*>(ps);
+    const float2 nL = make_float2(pn[-1], n0.x), nR = make_float2(n0.y, pn[2]);
+    const float2 sL = make_float2(ps[-1], s0.x), sR = make_float2(s0.y, ps[2]);
+    const float2 cL = make_float2(pc[-1], c0.x), cR = make_float2(c0.y, pc[2]);
+    // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
+    const float2 gpx = pfma(psub(cR, cL), pk(1.0f / 3.0f), pmul(padd(psub(nR, nL), psub(sR, sL)), pk(1.0f / 12.0f)));
+    const float2 gpy = pfma(psub(n0, s0), pk(1.0f / 3.0f), pmul(padd(psub(nR, sR), psub(nL, sL)), pk(1.0f / 12.0f)));
+    const float2 h = padd(dh, pk(C.href));
+    // Eqs. (force), (forcefric), (alphafric): nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
+    const float2 den = pfma(h, pfma(pk(2.0f), h, pk(6.0f * C.delta)), pk(3.0f * C.delta * C.delta));
+    const float2 fr = make_float2(__fdividef(C.nu6, den.x), __fdividef(C.nu6, den.y));
+    const float2 Fx = psub(pmul(h, psub(pk(C.gx), gpx)), pmul(fr, jx));
+    const float2 Fy = psub(pmul(h, psub(pk(C.gy), gpy)), pmul(fr, jy));
+    // Eq. (equilibria) with e^2 = 1 as S +- D per opposite pair; source 3 w_l c_l . F
+    const float2 ux = pmul(jx, ih), uy = pmul(jy, ih);
+    const float2 A = pmul(pmul(h, psub(pmul(pk(C.g), h), pfma(ux, ux, pmul(uy, uy)))), pk(1.0f / 6.0f));
+    const float2 Sx = pfma(pk(0.5f), pmul(jx, ux), A);
+    const float2 Sy = pfma(pk(0.5f), pmul(jy, uy), A);
+    const float2 a = padd(ux, uy), b = psub(uy, ux);
+    const float2 Sa = pmul(pfma(pk(0.5f), pmul(h, pmul(a, a)), A), pk(0.25f));
+    const float2 Sb = pmul(pfma(pk(0.5f), pmul(h, pmul(b, b)), A), pk(0.25f));
+    float2 o1, o2, o3, o4, o5, o6, o7, o8;
+    if constexpr (OMEGA1) {
+        const float2 Dx = pmul(padd(jx, Fx), pk(1.0f / 3.0f));
+        const float2 Dy = pmul(padd(jy, Fy), pk(1.0f / 3.0f));
+        const float2 Da = pmul(padd(padd(jx, jy), padd(Fx, Fy)), pk(1.0f / 12.0f));
+        const float2 Db = pmul(padd(psub(jy, jx), psub(Fy, Fx)), pk(1.0f / 12.0f));
+        o1 = padd(Sx, Dx); o5 = psub(Sx, Dx);
+        o3 = padd(Sy, Dy); o7 = psub(Sy, Dy);
+        o2 = padd(Sa, Da); o6 = psub(Sa, Da);
+        o4 = padd(Sb, Db); o8 = psub(Sb, Db);
+    } else {
+        const float2 w = pk(C.omega), m = pk(1.0f - C.omega);
+        const float2 Dx = pmul(jx, pk(1.0f / 3.0f)), Dy = pmul(jy, pk(1.0f / 3.0f));
+        const float2 Da = pmul(padd(jx, jy), pk(1.0f / 12.0f)), Db = pmul(psub(jy, jx), pk(1.0f / 12.0f));
+        const float2 Qx = pmul(Fx, pk(1.0f / 3.0f)), Qy = pmul(Fy, pk(1.0f / 3.0f));
+        const float2 Qa = pmul(padd(Fx, Fy), pk(1.0f / 12.0f)), Qb = pmul(psub(Fy, Fx), pk(1.0f / 12.0f));
+        o1 = padd(pfma(m, f[0 * fstride], pmul(w, padd(Sx, Dx))), Qx);
+        o5 = psub(pfma(m, f[4 * fstride], pmul(w, psub(Sx, Dx))), Qx);
+        o3 = padd(pfma(m, f[2 * fstride], pmul(w, padd(Sy, Dy))), Qy);
+        o7 = psub(pfma(m, f[6 * fstride], pmul(w, psub(Sy, Dy))), Qy);
+        o2 = padd(pfma(m, f[1 * fstride], pmul(w, padd(Sa, Da))), Qa);
+        o6 = psub(pfma(m, f[5 * fstride], pmul(w, psub(Sa, Da))), Qa);
+        o4 = padd(pfma(m, f[3 * fstride], pmul(w, padd(Sb, Db))), Qb);
+        o8 = psub(pfma(m, f[7 * fstride], pmul(w, psub(Sb, Db))), Qb);
+    }
+    // stored rest population f*_0 - href = (h - href) - sum_{l>0} f*_l, with
+    // the exact residuals folded back as in collide_store
+    V* om = reinterpret_cast<V*>(foutm) + (i >> 1);
+    const int hp = plane >> 1;
+    if constexpr (!NARROW) {
+        const float2 osum = padd(padd(padd(o1, o5), padd(o3, o7)), padd(padd(o2, o6), padd(o4, o8)));
+        float2 o0v, e2;
+        ptwo_sum(dh, make_float2(-osum.x, -osum.y), o0v, e2);
+        const float2 half_r = pmul(padd(er, e2), pk(0.5f));
+        o1 = padd(o1, half_r);
+        o5 = padd(o5, half_r);
+        reinterpret_cast<float2*>(fout0)[i >> 1] = o0v;
+        om[0] = o1; om[hp] = o2; om[2 * hp] = o3; om[3 * hp] = o4;
+        om[4 * hp] = o5; om[5 * hp] = o6; om[6 * hp] = o7; om[7 * hp] = o8;
+    } else {
+        const float Rax = C.r_axis, Rdg = C.r_diag, NRa = C.nr_axis, NRd = C.nr_diag;
+        const V q3 = narrow_pair<SM>(o3, Rax, NRa, C);
+        const V q5 = narrow_pair<SM>(o5, Rax, NRa, C);
+        const V q7 = narrow_pair<SM>(o7, Rax, NRa, C);
+        const V q2 = narrow_pair<SM>(o2, Rdg, NRd, C);
+        const V q4 = narrow_pair<SM>(o4, Rdg, NRd, C);
+        const V q6 = narrow_pair<SM>(o6, Rdg, NRd, C);
+        const V q8 = narrow_pair<SM>(o8, Rdg, NRd, C);
+        const float2 osum = padd(padd(padd(o1, o5), padd(o3, o7)), padd(padd(o2, o6), padd(o4, o8)));
+        // the last residual goes to the finer of the two roundings: the 16-bit
+        // one of f_1 - R or the FP32 one of f_0 - href (see collide_store)
+        constexpr float kRatio = std::is_same<SM, __half>::value ? 8192.0f : 65536.0f;
+        const bool lx = fabsf(o1.x - Rax) * kRatio < fabsf(dh.x - osum.x);
+        const bool ly = fabsf(o1.y - Rax) * kRatio < fabsf(dh.y - osum.y);
+        float2 o1r = o1;
+        const V q1r = narrow_pair<SM>(o1r, Rax, NRa, C);
+        const float2 adj = psub(o1r, o1);
+        const float2 os = make_float2(lx ? osum.x : osum.x + adj.x, ly ? osum.y : osum.y + adj.y);
+        float2 o0v, e2, o0n, e3;
+        ptwo_sum(dh, make_float2(-os.x, -os.y), o0v, e2);
+        ptwo_sum(o0v, padd(er, e2), o0n, e3);
+        float2 o1l = padd(o1, e3);
+        const V q1l = narrow_pair<SM>(o1l, Rax, NRa, C);
+        const uint32_t mask = (lx ? 0x0000ffffu : 0u) | (ly ? 0xffff0000u : 0u);
+        const V q1 = from_bits<V>((bits(q1l) & mask) | (bits(q1r) & ~mask));
+        reinterpret_cast<float2*>(fout0)[i >> 1] = o0n;
+        om[0] = q1; om[hp] = q2; om[2 * hp] = q3; om[3 * hp] = q4;
+        om[4 * hp] = q5; om[5 * hp] = q6; om[6 * hp] = q7; om[7 * hp] = q8;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy staging of the paired kernel: per march step, every plane's row
+// segment covering the CTA's columns and one pair beyond each side (and the
+// kappa row when theta varies) is copied into one of kPairStages shared
+// stages by cp.async.bulk, completion on the stage's mbarrier.
+constexpr int kPairStages = 4;
+
+template <typename SM, int BX, bool KFIELD>
+struct PairStage {
+    static constexpr int NC = 2 * BX;
+    static constexpr int A = 16 / (sizeof(SM) < 4 ? sizeof(SM) : 4);  // elements per 16 bytes
+    static constexpr int LMAX = NC + 24;  // >= the widest aligned segment, NC + 18
+    static constexpr int B0 = LMAX * 4;   // plane 0 (float)
+    static constexpr int BM = LMAX * (int)sizeof(SM);
+    static constexpr int BK = KFIELD ? LMAX * 4 : 0;
+    static constexpr int STAGE = (B0 + 8 * BM + BK + 127) / 128 * 128;
+    static constexpr int BYTES = kPairStages * STAGE;
+    static_assert(B0 % 16 == 0 && BM % 16 == 0, "stage planes must stay 16-byte aligned");
+};
+
+// Issued by warp 0 for the lattice row `row`: lane 0 arms the stage's
+// mbarrier with the byte count, lane l < 9 copies plane l from row
+// row - c_ly, lane 9 the kappa row; columns [a0, a1) of the periodic row,
+// in up to three pieces (nx a multiple of 8 keeps every piece aligned).
+template <typename SM>
+__device__ __noinline__ void issue_pair_row(unsigned char* stage, uint64_t* bar, const float* fin0, const SM* finm,
+                                            const float* kappa, int plane, int pitch, int nx, int ny, int row,
+                                            int a0, int a1, int b0, int bm, uint32_t bytes)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_arrive_tx(bar, bytes);
+    __syncwarp();
+    const int np = kappa ? 10 : 9;
+    if (lane < np) {
+        // c_ly of population l: 0 0 1 1 1 0 -1 -1 -1 (kappa: its own row)
+        const int cy = (lane >= 2 && lane <= 4) ? 1 : ((lane >= 6 && lane <= 8) ? -1 : 0);
+        int r = row - cy;
+        r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const char* src;
+        int es;
+        unsigned char* dst;
+        if (lane == 0) {
+            src = reinterpret_cast<const char*>(fin0 + (long long)r * pitch);
+            es = 4;
+            dst = stage;
+        } else if (lane < 9) {
+            src = reinterpret_cast<const char*>(finm + ((long long)(lane - 1) * plane + (long long)r * pitch));
+            es = (int)sizeof(SM);
+            dst = stage + b0 + (lane - 1) * bm;
+        } else {
+            src = reinterpret_cast<const char*>(kappa + (long long)r * nx);
+            es = 4;
+            dst = stage + b0 + 8 * bm;
+        }
+        int c = a0;
+        if (c < 0) {  // left periodic image
+            bulk_g2s(dst, src + (long long)(c + nx) * es, (uint32_t)(-c * es), bar);
+            dst += -c * es;
+            c = 0;
+        }
+        const int e = a1 < nx ? a1 : nx;
+        bulk_g2s(dst, src + (long long)c * es, (uint32_t)((e - c) * es), bar);
+        dst += (e - c) * es;
+        if (a1 > nx) bulk_g2s(dst, src, (uint32_t)((a1 - nx) * es), bar);  // right image
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One CTA of BX threads covers NC = 2 BX consecutive columns x0-2 .. x0+NC-3
+// (thread t: local columns j = 2t, 2t+1) and marches down a band of rows;
+// neighbouring CTAs overlap by 4 columns and each stores NC - 4.  The march
+// is step_band's: step k forms h of row r(k) into a 4-row shared ring, one
+// barrier, then the pressure of row r(k-1) and force, collision and store of
+// row r(k-3).  The pulled values of row r(k) come either from registers
+// loaded one row ahead plus warp shuffles (TMA = false), or from a shared
+// stage filled by bulk copies kPairStages rows ahead (TMA = true).
+template <typename SM, int BX, bool OMEGA1, bool KFIELD, bool TMA>
+__device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const SM* __restrict__ finm,
+                                           float* __restrict__ fout0, SM* __restrict__ foutm,
+                                           const float* __restrict__ kappa, const Geom& G,
+                                           const Consts<float>& C, int strip, int band, int nbands,
+                                           unsigned char* stage_mem)
+{
+    using IO = PairIO<SM>;
+    using V = typename IO::V;
+    using L = PairStage<SM, BX, KFIELD>;
+    constexpr int NC = 2 * BX;  // columns per CTA
+    constexpr int W = NC - 4;   // output columns per CTA
+    constexpr int OFF = 2;      // ring slot of local column j is OFF + j (keeps pairs 8-byte aligned)
+    __shared__ __align__(16) float hsm[4][NC + 4];  // h - href
+    __shared__ __align__(16) float psm[4][NC + 4];  // film pressure
+    // general tau: the eight pulled moving populations of the last four rows
+    __shared__ __align__(16) float2 fsm[OMEGA1 ? 1 : 4][8][OMEGA1 ? 1 : BX];
+    __shared__ __align__(8) uint64_t bars[TMA ? kPairStages : 1];
+
+    const int t = threadIdx.x, lane = t & 31;
+    const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
+    const int x0 = strip * W;
+    const int weff = min(W, nx - x0);     // output columns of this CTA (even)
+    const bool hcol = 2 * t <= weff + 3;  // h needed at local columns 0 .. weff+3
+    const bool pcol = 2 * t <= weff + 2;  // p needed at local columns 1 .. weff+2
+    const bool ocol = t >= 1 && 2 * t <= weff;
+    const int ybeg = (int)(((long long)band * ny) / nbands);
+    const int yend = (int)(((long long)(band + 1) * ny) / nbands);
+    const int dir = (band & 1) ? -1 : 1;
+    const int R = yend - ybeg;
+    const int rstart = dir > 0 ? ybeg - 2 : yend + 1;
+    const bool disj = KFIELD || C.kappa_u != 0.0f;
+    const float Rax = C.r_axis, Rdg = C.r_diag;
+    const int c = wrap_index(x0 - 2 + 2 * t, nx);  // own pair (even)
+
+    // ---- per-thread loads: registers of the row in flight
+    const bool edge = lane == 0 || lane == 31;
+    const int ce = lane == 0 ? wrap_index(c - 2, nx) : (c + 2 == nx ? 0 : c + 2);
+    // moving planes (index l - 1) a warp-edge lane reads at its outer
+    // neighbour pair, from rows y, y-1, y+1: lane 0 needs l = 1, 2, 8
+    // (arriving from the left), lane 31 needs l = 5, 4, 6 (from the right)
+    const int e0 = (lane == 0 ? 0 : 4) * plane;
+    const int e1 = (lane == 0 ? 1 : 3) * plane;
+    const int e2 = (lane == 0 ? 7 : 5) * plane;
+    const float2* __restrict__ f0p = reinterpret_cast<const float2*>(fin0);
+    const V* __restrict__ fmp = reinterpret_cast<const V*>(finm);
+    const int half = plane >> 1;  // pairs per plane (pitch is even)
+    float2 q0;
+    V qm[8], qe[3];
+
+    // ---- bulk copies: the row segment [a0, a1) per plane; column X at X - a0
+    const int a0 = floor_div(x0 - 4, L::A) * L::A;
+    const int a1 = (x0 + weff + 4 + L::A - 1) / L::A * L::A;
+    const int col = x0 - 2 + 2 * t - a0;
+    const uint32_t bytes_step = (uint32_t)(a1 - a0) * (uint32_t)(4 + 8 * sizeof(SM) + (KFIELD ? 4 : 0));
+    auto issue = [&](int j) {  // march step j (h row r(j)) into stage j % kPairStages
+        const int st = j & (kPairStages - 1);
+        issue_pair_row<SM>(stage_mem + st * L::STAGE, &bars[st], fin0, finm, KFIELD ? kappa : nullptr, plane,
+                           pitch, nx, ny, wrap_index(rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step);
+    };
+    bool gave_up = false;  // this thread stopped waiting for a stage (TMA)
+
+    // wrapped rows r(k-1), r(k), r(k+1), r(k+2)
+    int wm1 = wrap_index(rstart - dir, ny), w0 = wrap_index(rstart, ny);
+    int w1 = wrap_index(rstart + dir, ny), w2 = wrap_index(rstart + 2 * dir, ny);
+    auto load_row = [&](int wb, int w, int wa) {
+        const int ys = dir > 0 ? wb : wa, yn = dir > 0 ? wa : wb;  // rows y-1, y+1
+        const int i0 = (w * pitch + c) >> 1, is = (ys * pitch + c) >> 1, in = (yn * pitch + c) >> 1;
+        q0 = ldpair(f0p + i0);
+        qm[0] = ldpair(fmp + i0);               // l = 1 from row y
+        qm[1] = ldpair(fmp + (half + is));      // l = 2 from row y-1
+        qm[2] = ldpair(fmp + (2 * half + is));  // l = 3
+        qm[3] = ldpair(fmp + (3 * half + is));  // l = 4
+        qm[4] = ldpair(fmp + (4 * half + i0));  // l = 5 from row y
+        qm[5] = ldpair(fmp + (5 * half + in));  // l = 6 from row y+1
+        qm[6] = ldpair(fmp + (6 * half + in));  // l = 7
+        qm[7] = ldpair(fmp + (7 * half + in));  // l = 8
+        if (edge) {
+            qe[0] = ldpair(fmp + ((e0 + w * pitch + ce) >> 1));
+            qe[1] = ldpair(fmp + ((e1 + ys * pitch + ce) >> 1));
+            qe[2] = ldpair(fmp + ((e2 + yn * pitch + ce) >> 1));
+        }
+    };
+
+    float2 kap_n = pk(C.kappa_u);
+    if constexpr (TMA) {
+        if (t == 0) {
+#pragma unroll
+            for (int s = 0; s < kPairStages; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (t < 32)
+            for (int j = 0; j < kPairStages && j <= R + 3; ++j) issue(j);
+        if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
+    } else {
+        load_row(wm1, w0, w1);
+        if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
+    }
+
+    float2 jxv[4], jyv[4], ihv[4], erv[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) jxv[s] = jyv[s] = ihv[s] = erv[s] = pk(0.0f);
+    // ring slots no thread writes (outer halves of the edge columns' stencils)
+    if (t < 4) {
+        const int j = t < 2 ? t : NC + t;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) hsm[s][j] = psm[s][j] = 0.0f;
+    }
+
+    // one march step; false when the CTA gave up waiting for a bulk copy
+    auto body = [&](auto stage_c, int k) -> bool {
+        constexpr int s = decltype(stage_c)::value;  // ring slot of row r(k)
+        constexpr int s1 = (s + 3) & 3;              // r(k-1)
+        constexpr int s2 = (s + 2) & 3;              // r(k-2)
+        constexpr int s3 = (s + 1) & 3;              // r(k-3)
+        const float2 kap = kap_n;                    // kappa of row r(k-1)
+        // ---- (A) h, j of row r(k)
+        if (k <= R + 3) {
+            float2 f0, n[8];  // f_0 - href and the moving populations arriving at the pair
+            bool have = true;
+            if constexpr (TMA) {
+                have = hcol;
+                if (hcol) {
+                    const uint32_t parity = (uint32_t)(k / kPairStages) & 1u;
+                    if (C.wait_limit <= 0) {
+                        have = false;
+                    } else {
+                        int it = 0;
+                        while (!mbar_test(&bars[s], parity)) {
+                            if (++it >= C.wait_limit) {
+                                have = false;
+                                break;
+                            }
+                        }
+                    }
+                    gave_up = !have;
+                }
+                if (have) {
+                    const unsigned char* base = stage_mem + s * L::STAGE;
+                    const float* p0 = reinterpret_cast<const float*>(base);
+                    const SM* pm = reinterpret_cast<const SM*>(base + L::B0);
+                    constexpr int M = L::LMAX;
+                    auto own = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col),
+                                                                   (m & 1) ? Rdg : Rax, C); };
+                    auto left = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col - 2),
+                                                                    (m & 1) ? Rdg : Rax, C).y; };
+                    auto right = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col + 2),
+                                                                     (m & 1) ? Rdg : Rax, C).x; };
+                    f0 = *reinterpret_cast<const float2*>(p0 + col);
+                    const float2 o1 = own(0), o2 = own(1), o4 = own(3), o5 = own(4), o6 = own(5), o8 = own(7);
+                    n[0] = make_float2(left(0), o1.x);
+                    n[1] = make_float2(left(1), o2.x);
+                    n[2] = own(2);
+                    n[3] = make_float2(o4.y, right(3));
+                    n[4] = make_float2(o5.y, right(4));
+                    n[5] = make_float2(o6.y, right(5));
+                    n[6] = own(6);
+                    n[7] = make_float2(left(7), o8.x);
+                    if (KFIELD && pcol)
+                        kap_n = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base + L::B0 + 8 * L::BM) + col);
+                }
+            } else {
+                f0 = q0;
+                float2 v[8];
+#pragma unroll
+                for (int l = 0; l < 8; ++l) v[l] = decode_pair<SM>(qm[l], (l & 1) ? Rdg : Rax, C);
+                float ex = 0.f, ey = 0.f, ez = 0.f;  // left column of lane 0 / right column of lane 31
+                if (edge) {
+                    const float2 a = decode_pair<SM>(qe[0], Rax, C);  // l = 1 or 5: axis
+                    const float2 b = decode_pair<SM>(qe[1], Rdg, C);  // l = 2 or 4: diagonal
+                    const float2 d = decode_pair<SM>(qe[2], Rdg, C);  // l = 8 or 6: diagonal
+                    ex = lane == 0 ? a.y : a.x;
+                    ey = lane == 0 ? b.y : b.x;
+                    ez = lane == 0 ? d.y : d.x;
+                }
+                // the loads of row r(k+1) go out before this row's arithmetic
+                if (k + 1 <= R + 3) load_row(w0, w1, w2);
+                if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)w0 * nx + c));
+                // l = 1, 2, 8 arrive from the left, l = 4, 5, 6 from the right
+                float u1 = __shfl_up_sync(0xffffffffu, v[0].y, 1);
+                float u2 = __shfl_up_sync(0xffffffffu, v[1].y, 1);
+                float u8 = __shfl_up_sync(0xffffffffu, v[7].y, 1);
+                float d5 = __shfl_down_sync(0xffffffffu, v[4].x, 1);
+                float d4 = __shfl_down_sync(0xffffffffu, v[3].x, 1);
+                float d6 = __shfl_down_sync(0xffffffffu, v[5].x, 1);
+                if (lane == 0) { u1 = ex; u2 = ey; u8 = ez; }
+                if (lane == 31) { d5 = ex; d4 = ey; d6 = ez; }
+                n[0] = make_float2(u1, v[0].x);
+                n[1] = make_float2(u2, v[1].x);
+                n[2] = v[2];
+                n[3] = make_float2(v[3].y, d4);
+                n[4] = make_float2(v[4].y, d5);
+                n[5] = make_float2(v[5].y, d6);
+                n[6] = v[6];
+                n[7] = make_float2(u8, v[7].x);
+            }
+            if (have) {
+                float2 dh, er, jx, jy;
+                pair_moments(n, f0, dh, er, jx, jy);
+                *reinterpret_cast<float2*>(&hsm[s][OFF + 2 * t]) = dh;
+                erv[s] = er;
+                jxv[s] = jx;
+                jyv[s] = jy;
+                if constexpr (!OMEGA1) {
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) fsm[s][l][t] = n[l];
+                }
+            }
+        }
+        if constexpr (TMA) {
+            // every thread is done with this stage (or the CTA gives up)
+            if (__syncthreads_or(gave_up)) return false;
+            if (t < 32 && k + kPairStages <= R + 3) issue(k + kPairStages);
+        } else {
+            __syncthreads();
+        }
+        // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
+        if (pcol && k >= 2 && k <= R + 3) {
+            float2 ih;
+            const float2 p = pair_pressure(hsm[s] + OFF + 2 * t, hsm[s1] + OFF + 2 * t, hsm[s2] + OFF + 2 * t, kap,
+                                           disj, C, ih);
+            ihv[s1] = ih;
+            *reinterpret_cast<float2*>(&psm[s1][OFF + 2 * t]) = p;
+        }
+        // ---- (B2) force, collision and store of row r(k-3)
+        if (ocol && k >= 5) {
+            const int o = rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
+            const float* pn = (dir > 0 ? psm[s2] : psm[s]) + OFF + 2 * t;  // row o+1
+            const float* pc = psm[s3] + OFF + 2 * t;
+            const float* ps = (dir > 0 ? psm[s] : psm[s2]) + OFF + 2 * t;  // row o-1
+            const float2 dh = *reinterpret_cast<const float2*>(&hsm[s3][OFF + 2 * t]);
+            const float2* fp = nullptr;
+            if constexpr (!OMEGA1) fp = &fsm[s3][0][t];
+            pair_collide_store<SM, OMEGA1>(pn, pc, ps, dh, ihv[s3], jxv[s3], jyv[s3], erv[s3], fp, BX, fout0,
+                                           foutm, o * pitch + c, plane, C);
+        }
+        wm1 = w0;
+        w0 = w1;
+        w1 = w2;
+        w2 += dir;
+        w2 = w2 == ny ? 0 : (w2 < 0 ? ny - 1 : w2);
+        return true;
+    };
+
+    const int last = R + 4;
+    int k = 0;
+    bool ok = true;
+    for (;;) {
+        if (!(ok = body(std::integral_constant<int, 0>{}, k))) break;
+        if (++k > last) break;
+        if (!(ok = body(std::integral_constant<int, 1>{}, k))) break;
+        if (++k > last) break;
+        if (!(ok = body(std::integral_constant<int, 2>{}, k))) break;
+        if (++k > last) break;
+        if (!(ok = body(std::integral_constant<int, 3>{}, k))) break;
+        if (++k > last) break;
+    }
+    if constexpr (TMA) {
+        if (!ok && t == 0) {
+            // report, then wait (bounded) for the copies still in flight
+            // before the CTA's shared memory is released: the last march step
+            // issued is jmax; stage s holds at most one unfinished phase, its
+            // last issued step
+            if (C.status) atomicOr(C.status, kStatusTimeout);
+            const int jmax = min(k + kPairStages - 1, R + 3);
+            for (int s = 0; s < kPairStages; ++s) {
+                if (jmax < s) continue;
+                const int jl = jmax - ((jmax - s) % kPairStages);
+                int it = 0;
+                while (!mbar_test(&bars[s], (uint32_t)(jl / kPairStages) & 1u) && ++it < kWaitLimit) {
+                }
+            }
+        }
+    }
+}
+
+template <typename SM, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, 512 / BX)
+k_step2(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __restrict__ fout0,
+        SM* __restrict__ foutm, const float* __restrict__ kappa, const Geom G, const Consts<float> C)
+{
+    step_band2<SM, BX, OMEGA1, KFIELD, false>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
+                                              gridDim.y, nullptr);
+}
+
+template <typename SM, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, 512 / BX)
+k_step2_tma(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __restrict__ fout0,
+            SM* __restrict__ foutm, const float* __restrict__ kappa, const Geom G, const Consts<float> C)
+{
+    extern __shared__ __align__(128) unsigned char pair_stage_mem[];
+    step_band2<SM, BX, OMEGA1, KFIELD, true>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
+                                             gridDim.y, pair_stage_mem);
+}
+
+// ---------------------------------------------------------------------------
+// Launch of the paired kernels: block_x is the CTA width in columns (64, 128
+// or 256), i.e. block_x / 2 threads.
+
+template <typename SM, int BX, bool OM1, bool KF>
+cudaError_t pair_one(bool tma, dim3 grid, const float* fin0, const SM* finm, float* fout0, SM* foutm,
+                     const float* kappa, const Geom& G, const Consts<float>& C, cudaStream_t st)
+{
+    if (tma) {
+        using L = PairStage<SM, BX, KF>;
+        static bool attr = false;  // one attribute call per instantiation
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_step2_tma<SM, BX, OM1, KF>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_step2_tma<SM, BX, OM1, KF><<<grid, BX, L::BYTES, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+    } else {
+        k_step2<SM, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+    }
+    return cudaGetLastError();
+}
+
+template <typename SM, int BX>
+cudaError_t launch_pair_bx(bool tma, const float* fin0, const SM* finm, float* fout0, SM* foutm,
+                           const float* kappa, const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
+{
+    int bands = (G.ny + rows - 1) / rows;
+    if (bands > 65535) bands = 65535;
+    constexpr int W = 2 * BX - 4;
+    dim3 grid((G.nx + W - 1) / W, bands);
+    const bool om1 = C.omega == 1.0f;
+    if (kappa) {
+        if (om1) return pair_one<SM, BX, true, true>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+        return pair_one<SM, BX, false, true>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+    }
+    if (om1) return pair_one<SM, BX, true, false>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+    return pair_one<SM, BX, false, false>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+}
+
+template <typename SM>
+cudaError_t launch_pair(bool tma, int block_x, const float* fin0, const SM* finm, float* fout0, SM* foutm,
+                        const float* kappa, const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
+{
+    switch (block_x) {
+        case 64: return launch_pair_bx<SM, 32>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
+        case 128: return launch_pair_bx<SM, 64>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
+        case 256: return launch_pair_bx<SM, 128>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename SM, int BX, bool OM1, bool KF>
+int bps_pair_one(bool tma)
+{
+    int n = 0;
+    cudaError_t e;
+    if (tma) {
+        using L = PairStage<SM, BX, KF>;
+        cudaFuncSetAttribute(k_step2_tma<SM, BX, OM1, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_tma<SM, BX, OM1, KF>, BX, L::BYTES);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<SM, BX, OM1, KF>, BX, 0);
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+template <typename SM>
+int blocks_per_sm_pair(bool tma, int block_x, bool omega1, bool kfield)
+{
+    auto pick = [&](auto bx_c) {
+        constexpr int BX = decltype(bx_c)::value;
+        if (kfield) return omega1 ? bps_pair_one<SM, BX, true, true>(tma) : bps_pair_one<SM, BX, false, true>(tma);
+        return omega1 ? bps_pair_one<SM, BX, true, false>(tma) : bps_pair_one<SM, BX, false, false>(tma);
+    };
+    switch (block_x) {
+        case 64: return pick(std::integral_constant<int, 32>{});
+        case 128: return pick(std::integral_constant<int, 64>{});
+        case 256: return pick(std::integral_constant<int, 128>{});
+        default: return 0;
+    }
+}
+
+}  // namespace tflbm

@@ -133,6 +133,31 @@ def test_gradient_matches_central_differences_inverse_design():
     assert worst <= 1e-4, worst
 
 
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-3), ("f16", 2e-2), ("bf16", 2e-2)])
+def test_reduced_precision_tape_gradient_matches_oracle(dtype, tol):
+    """dL/dtheta and dL/dh0 of the FP32 and 16-bit-storage tapes, element by
+    element, against the FP64 oracle's reverse sweep (inverse-design shape,
+    64^2, 200 steps, sqrt(T) checkpoints).  The FP32 tape differentiates the
+    FP32 scheme on its own trajectory: the gap is FP32 rounding carried
+    through 200 steps forward and back (bound 1e-3 of the largest entry).
+    With 16-bit storage the trajectory itself differs from FP64 by the 16-bit
+    roundings of the moving populations (2^-12 FP16, 2^-9 BF16 relative),
+    hence 2e-2."""
+    h0, th, tgt, p = inputs.inverse_design(64, seed=4)
+    T = 200
+    L_o, gth_o, gh0_o, _ = _oracle_grads(p, h0, th, T, tgt)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    hh = torch.tensor(h0, dtype=torch.float64, device="cuda", requires_grad=True)
+    tg = torch.tensor(tgt, device="cuda")
+    loss = 0.5 * ((evolve(theta, hh, p, T, dtype=dtype).double() - tg) ** 2).sum()
+    loss.backward()
+    gth = theta.grad.cpu().numpy()
+    gh0 = hh.grad.cpu().numpy()
+    assert np.abs(gth - gth_o).max() <= tol * np.abs(gth_o).max()
+    assert np.abs(gh0 - gh0_o).max() <= tol * np.abs(gh0_o).max()
+    assert abs(loss.item() - L_o) <= tol * abs(L_o)
+
+
 def test_fp32_gradient_close_to_fp64():
     h0, th, tgt, p = inputs.inverse_design(64, seed=2)
     T = 200

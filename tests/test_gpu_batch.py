@@ -92,11 +92,19 @@ def test_batch_parity_with_oracle(dtype, taus):
         f.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+# Sliding drops: BF16 keeps 8 significant bits against FP16's 11, so its
+# unit roundoff (2^-9) is 8 times FP16's (2^-12); on drops that slide, every
+# step's rounding of the momentum-carrying populations moves the contact
+# lines, and the error on h scales with that roundoff.  The BF16 bound for
+# moving contact lines is therefore the FP16 bound times 8.
+TOL_SLIDING = {"f32": 1e-5, "f16": 1e-3, "bf16": 8e-3}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_sliding_drop_sweep_parity(dtype):
     """The sliding-drop sweep reduced to four domains (192x96 and 256x128,
     drops of apex 14-19 on the h* precursor, Bo from 0.05 to 1), batched,
-    1000 steps: moving contact lines are where FP32 rounding grows fastest."""
+    1000 steps: moving contact lines are where rounding grows fastest."""
     specs = [(h0, None, dict(p, theta_uniform=float(th[0, 0])))
              for h0, th, p in inputs.sliding_drops(count=4, seed=1, lx_range=(128, 256))]
     films = make_films(specs, dtype)
@@ -105,7 +113,7 @@ def test_sliding_drop_sweep_parity(dtype):
         B.step(1000)
         for (h0, th, p), f, m in zip(specs, films, m0):
             ho = oracle_h(h0, th, p, 1000)
-            assert rel_linf(host_h(f), ho) <= TOL[dtype], (p["nx"], p["bond"])
+            assert rel_linf(host_h(f), ho) <= TOL_SLIDING[dtype], (p["nx"], p["bond"])
             assert abs(f.mass() - m) / m <= 1e-6
     for f in films:
         f.close()
@@ -197,7 +205,7 @@ def test_single_tuner_keeps_state_and_time(dtype):
     sim.step(5)
     before = sim.get_state().cpu().numpy()
     best = sim.tune(trial_steps=4)
-    assert best["block_x"] in (64, 128, 256) and best["pipeline"] in ((0, 1, 2) if dtype == "f32" else (0, 1))
+    assert best["block_x"] in (64, 128, 256) and best["pipeline"] in ((0, 1, 2, 3) if dtype == "f32" else (0, 1, 3))
     assert sim.launch == best
     assert np.array_equal(before, sim.get_state().cpu().numpy())
     assert sim.time == 5

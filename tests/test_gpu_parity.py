@@ -125,10 +125,10 @@ def test_parity_patterned_dewetting_256_fp32():
     assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
 
 
-@pytest.mark.parametrize("shape", [dict(block_x=64, rows=1), dict(block_x=64, rows=5),
-                                   dict(block_x=64, rows=7, graph_chunk=4),
-                                   dict(block_x=128, rows=64), dict(block_x=256, rows=17),
-                                   dict(block_x=128, rows=3, graph_chunk=4),
+@pytest.mark.parametrize("shape", [dict(block_x=64, rows=1, pipeline=1), dict(block_x=64, rows=5, pipeline=1),
+                                   dict(block_x=64, rows=7, graph_chunk=4, pipeline=1),
+                                   dict(block_x=128, rows=64, pipeline=1), dict(block_x=256, rows=17, pipeline=1),
+                                   dict(block_x=128, rows=3, graph_chunk=4, pipeline=1),
                                    dict(block_x=64, rows=9, pipeline=0),
                                    dict(block_x=128, rows=33, pipeline=0),
                                    dict(block_x=64, rows=1, pipeline=2),
@@ -150,7 +150,7 @@ def test_launch_shape_does_not_change_results(shape):
     a, b = ref.get_state(), other.get_state()
     torch.cuda.synchronize()
     d = (a - b).abs()
-    if shape["block_x"] == 64 and shape.get("pipeline", 1) == 1:
+    if shape["block_x"] == 64 and shape["pipeline"] == 1:
         assert torch.equal(a, b), (d.max().item(), (d > 0).sum().item())
     else:
         assert d.max().item() <= 1e-6 * a.abs().max().item()
@@ -312,7 +312,8 @@ def test_state_roundtrip_resumes_bitwise():
 def test_bulk_copy_pipeline_needs_nx_multiple_of_8():
     h0, th, p = inputs.small_random(300, 20, seed=1)
     sim = ThinFilm(p, h0, th)
-    assert sim.launch["pipeline"] == 1
+    assert sim.launch["pipeline"] == 1  # FP32: one column per thread
+    assert ThinFilm(p, h0, th, dtype="f16").launch["pipeline"] == 3  # 16-bit, nx even: two columns
     with pytest.raises(L.TfLbmError):
         sim.set_launch(pipeline=0)
     h0, th, p = inputs.small_random(304, 20, seed=1)
@@ -332,6 +333,39 @@ def test_parity_bulk_copy_pipeline(dtype, nx, ny):
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f16", "bf16"])
+@pytest.mark.parametrize("case", ["random", "pattern128"])
+def test_parity_printed_pi_sign(dtype, case):
+    """The printed sign of Eq. (pfilm), p = -gamma (lap h - Pi) (pi_sign =
+    -1), element by element against the oracle in every storage type: a
+    theta field on a thick noisy film (the printed sign destabilises only
+    films near the precursor thickness), and patterned dewetting at 128^2."""
+    if case == "random":
+        h0, th, p = inputs.small_random(96, 80, seed=31, amp=0.05)
+        p.update(tau=0.9, g=1e-4, gx_body=1e-5, delta=1.0, pi_sign=-1)
+        steps = 300
+    else:
+        h0, th, p = inputs.patterned_dewetting(128, seed=5)
+        p.update(pi_sign=-1)
+        steps = 1000
+    r = run_both(h0, th, p, steps, dtype)
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+    assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
+
+
+@pytest.mark.parametrize("block_x", [64, 128, 256])
+@pytest.mark.parametrize("tau", [0.7, 1.6])
+@pytest.mark.parametrize("nx,ny", [(37, 29), (300, 41), (130, 3)])
+def test_parity_async_copy_pipeline_general_tau(block_x, tau, nx, ny):
+    """FP32 async-copy kernel (pipeline 2) at tau != 1, where it keeps the
+    pulled populations of the last four rows in a per-thread shared ring
+    beside the copy ring, for every CTA width, against the oracle."""
+    h0, th, p = inputs.small_random(nx, ny, seed=nx + 5 * ny, amp=0.05)
+    p.update(tau=tau, g=2e-4, gx_body=2e-5, gy_body=-1e-5, delta=1.0)
+    r = run_both(h0, th, p, 200, "f32", launch=dict(pipeline=2, block_x=block_x, rows=7))
+    assert rel_linf(r["h"], r["ho"]) <= TOL["f32"]
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("nx,ny", [(37, 29), (130, 70), (3, 3), (2, 1), (200, 2)])
 @pytest.mark.parametrize("rows", [1, 2, 16])
@@ -341,6 +375,62 @@ def test_parity_async_copy_pipeline(dtype, nx, ny, rows):
     h0, th, p = inputs.small_random(nx, ny, seed=nx * 3 + ny, amp=0.05)
     p.update(tau=0.9 if dtype == "f64" else 1.0, g=2e-4, gx_body=2e-5, delta=1.0)
     r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=2, rows=rows))
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("pipeline", [3, 4])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("tau", [1.0, 0.75])
+@pytest.mark.parametrize("nx,ny,block_x", [(16, 9, 64), (64, 48, 64), (200, 33, 128), (304, 41, 256),
+                                           (520, 70, 128), (2, 5, 64)])
+def test_parity_paired_pipelines(pipeline, dtype, tau, nx, ny, block_x):
+    """The two-column kernels (3: per-thread loads and lane shuffles; 4:
+    rows staged by bulk copies) against the oracle, at both relaxation
+    kernels, every storage type they take and CTA widths of 64, 128 and 256
+    columns, including lattices narrower than one CTA (strips wrap on both
+    sides) and several strips with a ragged last one."""
+    if pipeline == 4 and nx % 8:
+        pytest.skip("bulk copies need nx a multiple of 8")
+    h0, th, p = inputs.small_random(nx, ny, seed=nx * 11 + ny, amp=0.05)
+    p.update(tau=tau, g=2e-4, gx_body=2e-5, gy_body=-1e-5, delta=1.0)
+    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=pipeline, block_x=block_x, rows=7))
+    assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
+    assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
+
+
+def test_paired_pipelines_agree_bitwise():
+    """Both two-column kernels compute every node with the same operations
+    in the same order (they differ only in how the pulled values reach the
+    thread), so their states are identical bit for bit."""
+    h0, th, p = inputs.small_random(304, 141, seed=19, amp=0.05)
+    p.update(tau=0.9, gx_body=1e-5)
+    states = []
+    for pipe in (3, 4):
+        sim = ThinFilm(p, h0, th)
+        sim.set_launch(pipeline=pipe, block_x=128, rows=13, graph_chunk=0)
+        sim.step(25)
+        states.append(sim.get_state())
+    assert torch.equal(states[0], states[1])
+
+
+@pytest.mark.parametrize("pipeline,dtype", [(0, "f32"), (0, "f16"), (4, "f32"), (4, "bf16")])
+def test_bulk_copy_wait_limit_reports_timeout(pipeline, dtype):
+    """A bulk-copy step kernel that gives up waiting for its own row copies
+    sets TF_LBM_STATUS_TIMEOUT, stops issuing, waits (bounded) for the copies
+    it has issued and returns.  A limit of 0 polls makes every wait give up
+    at once, deterministically, while every issued copy still lands.  The
+    context stays usable: a fresh run with the default limit then matches
+    the oracle."""
+    h0, th, p = inputs.small_random(64, 48, seed=2, amp=0.05)
+    sim = ThinFilm(p, h0, th, dtype=dtype)
+    sim.set_launch(pipeline=pipeline, graph_chunk=0)
+    assert sim.check() == 0
+    L.tf_lbm_set_wait_limit(sim.handle, 0)
+    sim.step(3)
+    assert sim.check() & L.TF_LBM_STATUS_TIMEOUT
+    L.tf_lbm_set_wait_limit(sim.handle, -1)
+    sim.close()
+    r = run_both(h0, th, p, 50, dtype, launch=dict(pipeline=pipeline))
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
 
 
@@ -458,7 +548,9 @@ def test_parity_random_configurations(case):
              hstar=float(rng.uniform(0.05, 0.1)), n_exp=nm[0], m_exp=nm[1],
              gx_body=float(rng.uniform(-1e-4, 1e-4)), gy_body=float(rng.uniform(-1e-4, 1e-4)))
     uniform = bool(rng.integers(0, 2))
-    r = run_both(h0, th, p, 60, dtype, theta_uniform=float(np.radians(rng.uniform(5, 45))) if uniform else None)
+    th_u = float(np.radians(rng.uniform(5, 45))) if uniform else None
+    p["pi_sign"] = int(rng.choice([1, -1]))
+    r = run_both(h0, th, p, 60, dtype, theta_uniform=th_u)
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype], (nx, ny, dtype, p)
     if dtype in ("f32", "f64"):
         assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]

@@ -68,3 +68,16 @@ def test_noalloc_sum_limits_and_empty_input():
     out.fill_(7.0)
     L.tf_lbm_sum_noalloc(0, 0, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert out.item() == 0.0
+
+
+def test_noalloc_sum_at_the_largest_accepted_size():
+    """n = TF_LBM_NOALLOC_MAX_ELEMS exactly: every one of the 4096 blocks is
+    full and the final kernel reduces the largest partial table.  A sum of
+    ones is exact in double precision; a smaller call right after it must
+    not see the large call's partials."""
+    n = L.TF_LBM_NOALLOC_MAX_ELEMS
+    x = torch.ones(n, dtype=torch.float64, device="cuda")  # 512 MB
+    assert _noalloc_sum(x) == float(n)
+    del x
+    y = torch.full((1000,), 0.25, dtype=torch.float64, device="cuda")
+    assert _noalloc_sum(y) == 250.0
