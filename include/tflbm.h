@@ -110,14 +110,12 @@ typedef struct tf_lbm_handle tf_lbm_handle;
  *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
  *            otherwise an even number >= 2);
  *   pipeline: 3 = every thread owns two adjacent columns, loads aligned
- *            pairs one row ahead, takes the values that cross a pair
- *            boundary from the neighbouring lane and computes both nodes
- *            with paired FP32 instructions (default when nx is even and the
- *            dtype is not TF_LBM_F64); 4 = as 3, but the row segments are
- *            staged in shared memory by bulk copies four rows ahead instead
- *            of per-thread loads (nx a multiple of 8, >= 16, not
- *            TF_LBM_F64); 1 = every thread loads its own column
- *            into registers, one row ahead (default otherwise); 2 = every
+ *            pairs one (FP32) or two (16-bit) rows ahead, takes the values
+ *            that cross a pair boundary from the neighbouring lane and
+ *            computes both nodes with paired FP32 instructions (nx even, not
+ *            TF_LBM_F64; default for TF_LBM_F16 and TF_LBM_BF16 when nx is
+ *            even); 1 = every thread loads its own column into registers,
+ *            one row ahead (default otherwise); 2 = every
  *            thread copies its own populations into shared memory by
  *            asynchronous copies, two rows ahead (TF_LBM_F32 and TF_LBM_F64
  *            only); 0 = row segments streamed into shared memory by bulk
@@ -183,7 +181,7 @@ int64_t tf_lbm_time(const tf_lbm_handle* H);
 int tf_lbm_get_launch(const tf_lbm_handle* H, tf_lbm_launch* out);
 int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in);
 
-/* How long a bulk-copy step kernel (pipelines 0 and 4) waits for one of its
+/* How long the bulk-copy step kernel (pipeline 0) waits for one of its
  * own row copies before giving up: `polls` tests of the copy's completion
  * barrier (polls < 0 restores the default, 2^22; polls == 0 gives up at
  * once).  A kernel that gives up sets TF_LBM_STATUS_TIMEOUT (tf_lbm_check),

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("n_exp", ctypes.c_int32), ("m_exp", ctypes.c_int32),
-        ("pi_sign", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("pi_sign", ctypes.c_int32), ("forcing", ctypes.c_int32),
         ("tau", ctypes.c_double), ("gamma", ctypes.c_double),
         ("g", ctypes.c_double), ("delta", ctypes.c_double),
         ("hstar", ctypes.c_double), ("gx_body", ctypes.c_double),
@@ -112,10 +112,14 @@ class Config:
     pi_sign: int = 1
     gx_body: float = 0.0
     gy_body: float = 0.0
+    # 0: Eq. (LBE) as printed (u = sum c f / h before collision, source
+    # 3 w_l c_l.F); 1: the labelled second-order-forcing alternative (see the
+    # header of tflbm_oracle.c), forward step only
+    forcing: int = 0
     extra: dict = field(default_factory=dict)
 
     def cparams(self) -> Params:
-        return Params(self.nx, self.ny, self.n_exp, self.m_exp, self.pi_sign, 0,
+        return Params(self.nx, self.ny, self.n_exp, self.m_exp, self.pi_sign, self.forcing,
                       self.tau, self.gamma, self.g, self.delta, self.hstar,
                       self.gx_body, self.gy_body)
 
@@ -229,6 +233,8 @@ def adjoint_step(cfg: Config, kap: np.ndarray, f_t: np.ndarray, a_next: np.ndarr
     """dL/df(t) from dL/df(t+1) for the step taken from the post-streaming
     state f_t; adds the step's contribution to grad_kappa (in place)."""
     kap = np.ascontiguousarray(np.broadcast_to(np.asarray(kap, np.float64), (cfg.ny, cfg.nx)))
+    if cfg.forcing != 0:
+        raise ValueError("the oracle adjoint differentiates Eq. (LBE) as printed (forcing = 0) only")
     f_t = np.ascontiguousarray(f_t, np.float64)
     a_next = np.ascontiguousarray(a_next, np.float64)
     assert grad_kappa.flags.c_contiguous and grad_kappa.dtype == np.float64

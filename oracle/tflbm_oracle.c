@@ -25,7 +25,16 @@
  *    Section II are then met exactly.
  *  - Eq. (LBE) source term: w_l (dt/c_s^2) c_l.F = 3 w_l c_l.F with c_s^2=1/3,
  *    no extra prefactor; the velocity in f_eq and in the friction is
- *    u = (sum_l c_l f_l)/h taken before collision.
+ *    u = (sum_l c_l f_l)/h taken before collision (forcing = 0, the
+ *    default).  forcing = 1 is a labelled alternative, not the paper's
+ *    printed equation: the second-order forcing used by many shallow-water
+ *    lattice Boltzmann schemes, with u = (sum_l c_l f_l + F/2)/h (the
+ *    friction -nu alpha u is then implicit: u (h + nu alpha/2) =
+ *    j + F'/2, F' the force without friction) and the source
+ *    (1 - omega/2) w_l [3 (c_l - u) + 9 (c_l.u) c_l].F, whose zeroth moment
+ *    is 0 and first moment (1 - omega/2) F, so that momentum again gains
+ *    exactly F per step.  It exists to compare the two readings against
+ *    the growth rates the paper reports (Sec. III A).
  *  - Eq. (pfilm) sign: the printed p = -gamma (lap h - Pi) makes the precursor
  *    film linearly unstable and gives no contact angle.  The physical reading
  *    p = -gamma (lap h + Pi) is the default (pi_sign = +1); pi_sign = -1
@@ -54,7 +63,7 @@ typedef struct {
     int32_t nx, ny;       /* periodic lattice, x fastest                     */
     int32_t n_exp, m_exp; /* exponents (n, m) of Eq. (disjoiningP)           */
     int32_t pi_sign;      /* +1: p = -gamma(lap h + Pi); -1: printed form    */
-    int32_t pad_;
+    int32_t forcing;      /* 0: Eq. (LBE) as printed; 1: second-order forcing */
     double tau;           /* BGK relaxation time, omega = 1/tau              */
     double gamma;         /* surface tension                                 */
     double g;             /* gravity in the equilibria (g < 0: hanging film) */
@@ -282,13 +291,40 @@ void orc_step(const orc_params* P, const double* kappa, double* f, int64_t nstep
         /* moments, pressure and force, all from time-t fields */
         orc_moments(P, f, h, ux, uy);
         pressure_force(P, kappa, h, ux, uy, lap, p, gpx, gpy, Fx, Fy);
-        /* collision: (1 - omega) f + omega f_eq + w_l (dt / c_s^2) c_l . F */
+        if (P->forcing == 1) {
+            /* second-order forcing: u = (j + F/2)/h with the friction taken at
+             * that velocity, u (h + nu alpha/2) = j + F'/2 */
+            const double nu = (P->tau - 0.5) / 3.0;
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < N; ++i) {
+                double jx = 0.0, jy = 0.0;
+                for (int l = 0; l < 9; ++l) { jx += CX[l] * f[l * N + i]; jy += CY[l] * f[l * N + i]; }
+                const double a = orc_alpha(h[i], P->delta);
+                const double fpx = -h[i] * gpx[i] + h[i] * P->gx_body;
+                const double fpy = -h[i] * gpy[i] + h[i] * P->gy_body;
+                ux[i] = (jx + 0.5 * fpx) / (h[i] + 0.5 * nu * a);
+                uy[i] = (jy + 0.5 * fpy) / (h[i] + 0.5 * nu * a);
+                Fx[i] = fpx - nu * a * ux[i];
+                Fy[i] = fpy - nu * a * uy[i];
+            }
+        }
+        /* collision: (1 - omega) f + omega f_eq + source */
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             double fe[9];
             orc_feq(P->g, h[i], ux[i], uy[i], fe);
             for (int l = 0; l < 9; ++l) {
-                double src = 3.0 * W[l] * (CX[l] * Fx[i] + CY[l] * Fy[i]);
+                double src;
+                if (P->forcing == 1) {
+                    /* (1 - omega/2) w_l [3 (c_l - u) + 9 (c_l.u) c_l] . F */
+                    const double cu = CX[l] * ux[i] + CY[l] * uy[i];
+                    const double cF = CX[l] * Fx[i] + CY[l] * Fy[i];
+                    const double uF = ux[i] * Fx[i] + uy[i] * Fy[i];
+                    src = (1.0 - 0.5 * omega) * W[l] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+                } else {
+                    /* w_l (dt / c_s^2) c_l . F of Eq. (LBE) */
+                    src = 3.0 * W[l] * (CX[l] * Fx[i] + CY[l] * Fy[i]);
+                }
                 fpost[l * N + i] = (1.0 - omega) * f[l * N + i] + omega * fe[l] + src;
             }
         }

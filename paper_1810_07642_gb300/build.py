@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, f"libtflbm_{platform.machine()}.so")
-SOURCES = ["tflbm_api.cu", "tflbm_aux.cu", "step_f32.cu", "step_f16.cu", "tflbm_adjoint.cu",
-           "tflbm_noalloc.cu", "tflbm_batch.cu"]
+SOURCES = ["tflbm_api.cu", "tflbm_aux.cu", "step_f32.cu", "step_f16.cu", "step2_f32.cu", "step2_f16.cu",
+           "step2_bf16.cu", "tflbm_adjoint.cu", "tflbm_noalloc.cu", "tflbm_batch.cu"]
 HEADERS = ["tflbm_internal.h", "tflbm_step.cuh", "tflbm_step2.cuh", "tflbm_handle.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -1,7 +1,6 @@
-// Instantiations of the fused step (tflbm_step.cuh and the paired-column
-// kernel of tflbm_step2.cuh) with the 8 moving populations stored in FP16 or
-// BF16 and all arithmetic in FP32.
-#include "tflbm_step2.cuh"
+// Instantiations of the one-column fused step (tflbm_step.cuh) with the 8
+// moving populations stored in FP16 or BF16 and all arithmetic in FP32.
+#include "tflbm_step.cuh"
 
 namespace tflbm {
 
@@ -14,8 +13,6 @@ static cudaError_t launch_n(const void* fin, void* fout, const void* kappa, cons
     float* g0 = (float*)fout;
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
     const float* k = (const float*)kappa;
-    if (is_pair_pipeline(S.pipeline))
-        return launch_pair<SM>(S.pipeline == kPipePairTma, S.block_x, f0, fm, g0, gm, k, G, C, S.rows, st);
     switch (S.block_x) {
         case 64: return launch_step_bx<SM, float, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
         case 128: return launch_step_bx<SM, float, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
@@ -36,7 +33,6 @@ cudaError_t launch_step_narrow(int store, const void* fin, void* fout, const voi
 template <typename SM>
 static int bps(int pipeline, int block_x, bool omega1, bool kfield)
 {
-    if (is_pair_pipeline(pipeline)) return blocks_per_sm_pair<SM>(pipeline == kPipePairTma, block_x, omega1, kfield);
     switch (block_x) {
         case 64: return blocks_per_sm_bx<SM, float, 64>(pipeline, omega1, kfield);
         case 128: return blocks_per_sm_bx<SM, float, 128>(pipeline, omega1, kfield);

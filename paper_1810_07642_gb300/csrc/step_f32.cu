@@ -1,7 +1,6 @@
-// FP32 and FP64 instantiations of the fused step (tflbm_step.cuh, and the
-// paired-column kernel of tflbm_step2.cuh for FP32) and the dispatch over
-// storage types.
-#include "tflbm_step2.cuh"
+// FP32 and FP64 instantiations of the one-column fused step (tflbm_step.cuh)
+// and the dispatch over storage types and pipelines.
+#include "tflbm_step.cuh"
 
 namespace tflbm {
 
@@ -20,9 +19,6 @@ static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, 
     T* g0 = (T*)fout;
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
     const T* k = (const T*)kappa;
-    if constexpr (std::is_same<T, float>::value)
-        if (is_pair_pipeline(S.pipeline))
-            return launch_pair<SM>(S.pipeline == kPipePairTma, S.block_x, f0, fm, g0, gm, k, G, C, S.rows, st);
     switch (S.block_x) {
         case 64: return launch_step_bx<SM, T, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
         case 128: return launch_step_bx<SM, T, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
@@ -35,6 +31,14 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
                         const Consts<float>* C32, const Consts<double>* C64, const Shape& S,
                         cudaStream_t st)
 {
+    if (S.pipeline == kPipePair) {
+        switch (store) {
+            case kStoreF32: return pair_step_f32(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
+            case kStoreF16: return pair_step_f16(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
+            case kStoreBF16: return pair_step_bf16(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (store) {
         case kStoreF32: return launch_typed<float, float>(fin, fout, kappa, G, *C32, S, st);
         case kStoreF64: return launch_typed<double, double>(fin, fout, kappa, G, *C64, S, st);
@@ -44,8 +48,14 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
 
 int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield)
 {
-    if (store == kStoreF32 && is_pair_pipeline(pipeline))
-        return blocks_per_sm_pair<float>(pipeline == kPipePairTma, block_x, omega1, kfield);
+    if (pipeline == kPipePair) {
+        switch (store) {
+            case kStoreF32: return pair_blocks_per_sm_f32(block_x, omega1, kfield);
+            case kStoreF16: return pair_blocks_per_sm_f16(block_x, omega1, kfield);
+            case kStoreBF16: return pair_blocks_per_sm_bf16(block_x, omega1, kfield);
+            default: return 0;
+        }
+    }
     if (store == kStoreF32 || store == kStoreF64) {
         const bool f = store == kStoreF32;
         switch (block_x) {

@@ -105,9 +105,9 @@ int store_of(int dtype)
     }
 }
 
-// Default launch shape: the two-column kernel where it applies, CTAs 256
-// columns wide on wide lattices (128 for the one-column kernels) and half
-// that otherwise, and a band height that makes the grid one full wave of
+// Default launch shape: the two-column kernel where it applies, CTAs 128
+// columns wide (one-column kernel on lattices narrower than 1024: 64), and
+// a band height that makes the grid one full wave of
 // resident CTAs (all bands do the same work, so a partial second wave would
 // idle most SMs), but no shorter than 16 rows: each band spends 5 warm-up rows.
 Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
@@ -119,7 +119,7 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
     // one-column kernel, which measured faster
     const int store = store_of(p.dtype);
     const bool pair = pair_pipeline_ok(G.nx, store) && (store == kStoreF16 || store == kStoreBF16);
-    s.block_x = pair ? (G.nx >= 1024 ? 256 : 128) : (G.nx >= 1024 ? 128 : 64);
+    s.block_x = (pair || G.nx >= 1024) ? 128 : 64;
     const int strips = (G.nx + s.block_x - 5) / (s.block_x - 4);  // CTAs overlap by 4 columns
     int sms = 152;
     int dev = 0;
@@ -451,15 +451,12 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return fail(H, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
     if (in->pipeline != kPipeTma && in->pipeline != kPipeLdg && in->pipeline != kPipeAsync &&
-        in->pipeline != kPipePair && in->pipeline != kPipePairTma)
+        in->pipeline != kPipePair)
         return fail(H, TF_LBM_ERR_ARG,
-                    "pipeline must be 0 (bulk copies), 1 (per-thread loads), 2 (per-thread async copies), "
-                    "3 (two columns per thread) or 4 (two columns per thread, bulk copies)");
+                    "pipeline must be 0 (bulk copies), 1 (per-thread loads), 2 (per-thread async copies) "
+                    "or 3 (two columns per thread)");
     if (in->pipeline == kPipePair && !pair_pipeline_ok(H->G.nx, H->desc.store))
         return fail(H, TF_LBM_ERR_ARG, "the two-column pipeline needs nx even and an FP32 compute type");
-    if (in->pipeline == kPipePairTma && !pair_tma_pipeline_ok(H->G.nx, H->desc.store))
-        return fail(H, TF_LBM_ERR_ARG,
-                    "the two-column bulk-copy pipeline needs nx a multiple of 8, >= 16, and an FP32 compute type");
     if (in->pipeline == kPipeAsync && H->msize != H->esize)
         return fail(H, TF_LBM_ERR_ARG, "the async-copy pipeline needs FP32 or FP64 storage");
     if (in->pipeline == kPipeTma && !tma_pipeline_ok(H->G.nx))

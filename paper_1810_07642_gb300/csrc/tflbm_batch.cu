@@ -298,11 +298,10 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
     std::vector<Shape> cands;
     for (int bx : {64, 128, 256}) {
         const int strips = strips_of(H->G.nx, bx);
-        for (int pipe : {kPipePair, kPipePairTma, kPipeLdg, kPipeAsync, kPipeTma}) {
+        for (int pipe : {kPipePair, kPipeLdg, kPipeAsync, kPipeTma}) {
             if (pipe == kPipeTma && !tma_pipeline_ok(H->G.nx)) continue;
             if (pipe == kPipeAsync && H->msize != H->esize) continue;
             if (pipe == kPipePair && !pair_pipeline_ok(H->G.nx, H->desc.store)) continue;
-            if (pipe == kPipePairTma && !pair_tma_pipeline_ok(H->G.nx, H->desc.store)) continue;
             const int occ = std::max(1, step_blocks_per_sm(H->desc.store, pipe, bx, om1, kf));
             std::vector<int> rows;
             for (int w = 1; w <= 3; ++w) {

@@ -18,12 +18,9 @@ struct Geom {
 constexpr int kPipeTma = 0;
 constexpr int kPipeLdg = 1;
 constexpr int kPipeAsync = 2;  // per-thread cp.async staging (full-width storage only)
-constexpr int kPipePair = 3;     // two columns per thread, per-thread loads (FP32 compute type, nx even)
-constexpr int kPipePairTma = 4;  // two columns per thread, rows staged by bulk copies (also nx % 8 == 0)
+constexpr int kPipePair = 3;   // two columns per thread (FP32 compute type, nx even)
 inline bool tma_pipeline_ok(int nx) { return nx % 8 == 0 && nx >= 16; }
 inline bool pair_pipeline_ok(int nx, int store) { return nx % 2 == 0 && store != 1 /* kStoreF64 */; }
-inline bool pair_tma_pipeline_ok(int nx, int store) { return pair_pipeline_ok(nx, store) && tma_pipeline_ok(nx); }
-inline bool is_pair_pipeline(int pipeline) { return pipeline == kPipePair || pipeline == kPipePairTma; }
 
 // Status bit a kernel sets when an mbarrier wait gave up (tf_lbm_check).
 constexpr int kStatusTimeout = 4;
@@ -72,6 +69,17 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
                         cudaStream_t st);
 // Resident CTAs per SM of the step kernel for a launch shape (0 if unknown).
 int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool kfield);
+// The two-column step (pipeline kPipePair) per storage type (step2_*.cu),
+// and its resident CTAs per SM.
+cudaError_t pair_step_f32(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
+                          const Consts<float>& C, int rows, cudaStream_t st);
+cudaError_t pair_step_f16(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
+                          const Consts<float>& C, int rows, cudaStream_t st);
+cudaError_t pair_step_bf16(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
+                           const Consts<float>& C, int rows, cudaStream_t st);
+int pair_blocks_per_sm_f32(int block_x, bool omega1, bool kfield);
+int pair_blocks_per_sm_f16(int block_x, bool omega1, bool kfield);
+int pair_blocks_per_sm_bf16(int block_x, bool omega1, bool kfield);
 
 // One work item of the batched step: a band of a strip of one domain.
 struct BatchItem {

@@ -32,6 +32,7 @@
 #include <cuda_fp16.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "tflbm_internal.h"
 
@@ -71,6 +72,38 @@ __device__ __forceinline__ T fdisj(T r, int n, int m)
 }
 
 template <typename S> __device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
+
+// Programmatic dependent launch.  A step kernel lets the next kernel of its
+// stream be scheduled as soon as all of its own CTAs have started (the next
+// step's CTAs then take SMs as this step's CTAs retire, instead of waiting
+// for a full launch), and waits for the previous kernel of the stream to
+// complete, with its writes visible, before it touches global memory.  Both
+// are hardware dependencies (no polling); without the launch attribute the
+// wait returns at once.
+__device__ __forceinline__ void dependent_launch_entry()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch `kern` with the programmatic-stream-serialization attribute (see
+// dependent_launch_entry).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t st,
+                             Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Element conversions of the moving-population storage types.
 __device__ __forceinline__ float to_f(float q) { return q; }
@@ -500,6 +533,7 @@ __global__ void __launch_bounds__(BX, sizeof(T) == 4 ? 1024 / BX : 1)
 k_step(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
        SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
+    dependent_launch_entry();
     step_band<SM, T, BX, OMEGA1, KFIELD, ASYNC>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x,
                                                 blockIdx.y, gridDim.y);
 }
@@ -533,6 +567,7 @@ __global__ void __launch_bounds__(BX, sizeof(T) == 4 ? 1024 / BX : 1)
 k_step_batch(const BatchItem* __restrict__ items, int nitems, const BatchDomain<T>* __restrict__ doms,
              int parity, int* queue)
 {
+    dependent_launch_entry();
     if (!queue) {
         batch_item<SM, T, BX, OMEGA1, KFIELD>(items[blockIdx.x], doms, parity);
         return;
@@ -667,6 +702,7 @@ __global__ void __launch_bounds__(BX, (OMEGA1 && sizeof(T) == 4) ? 1024 / BX : 1
 k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restrict__ fout0,
            SM* __restrict__ foutm, const T* __restrict__ kappa, const Geom G, const Consts<T> C)
 {
+    dependent_launch_entry();
     using L = TmaLayout<SM, T, BX>;
     extern __shared__ __align__(128) unsigned char stage_mem[];
     __shared__ T hsm[4][BX];  // h - href ring: slot t = column x0 - 2 + t
@@ -826,16 +862,15 @@ cudaError_t launch_one(int pipeline, dim3 grid, const T* fin0, const SM* finm, T
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_step_tma<SM, T, BX, OM1, KF><<<grid, BX, L::BYTES, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+        return launch_dependent(k_step_tma<SM, T, BX, OM1, KF>, grid, BX, L::BYTES, st, fin0, finm, fout0, foutm,
+                                kappa, G, C);
     } else if constexpr (std::is_same<SM, T>::value) {
         if (pipeline == kPipeAsync)
-            k_step<SM, T, BX, OM1, KF, true><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-        else
-            k_step<SM, T, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-    } else {
-        k_step<SM, T, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
+            return launch_dependent(k_step<SM, T, BX, OM1, KF, true>, grid, BX, 0, st, fin0, finm, fout0, foutm,
+                                    kappa, G, C);
+        return launch_dependent(k_step<SM, T, BX, OM1, KF>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
     }
-    return cudaGetLastError();
+    return launch_dependent(k_step<SM, T, BX, OM1, KF>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
 }
 
 template <typename SM, typename T, int BX>
@@ -864,8 +899,8 @@ cudaError_t batch_one(const BatchLaunch& L, cudaStream_t st)
         *L.query_occupancy = e == cudaSuccess ? n : 0;
         return e;
     }
-    k_step_batch<SM, T, BX, OM1, KF><<<L.grid, BX, 0, st>>>(L.items, L.nitems, d, L.parity, L.queue);
-    return cudaGetLastError();
+    return launch_dependent(k_step_batch<SM, T, BX, OM1, KF>, dim3(L.grid), BX, 0, st, L.items, L.nitems, d, L.parity,
+                            L.queue);
 }
 
 template <typename SM, typename T, int BX>

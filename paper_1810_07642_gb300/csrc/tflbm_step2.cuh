@@ -249,91 +249,23 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-copy staging of the paired kernel: per march step, every plane's row
-// segment covering the CTA's columns and one pair beyond each side (and the
-// kappa row when theta varies) is copied into one of kPairStages shared
-// stages by cp.async.bulk, completion on the stage's mbarrier.
-constexpr int kPairStages = 4;
-
-template <typename SM, int BX, bool KFIELD>
-struct PairStage {
-    static constexpr int NC = 2 * BX;
-    static constexpr int A = 16 / (sizeof(SM) < 4 ? sizeof(SM) : 4);  // elements per 16 bytes
-    static constexpr int LMAX = NC + 24;  // >= the widest aligned segment, NC + 18
-    static constexpr int B0 = LMAX * 4;   // plane 0 (float)
-    static constexpr int BM = LMAX * (int)sizeof(SM);
-    static constexpr int BK = KFIELD ? LMAX * 4 : 0;
-    static constexpr int STAGE = (B0 + 8 * BM + BK + 127) / 128 * 128;
-    static constexpr int BYTES = kPairStages * STAGE;
-    static_assert(B0 % 16 == 0 && BM % 16 == 0, "stage planes must stay 16-byte aligned");
-};
-
-// Issued by warp 0 for the lattice row `row`: lane 0 arms the stage's
-// mbarrier with the byte count, lane l < 9 copies plane l from row
-// row - c_ly, lane 9 the kappa row; columns [a0, a1) of the periodic row,
-// in up to three pieces (nx a multiple of 8 keeps every piece aligned).
-template <typename SM>
-__device__ __noinline__ void issue_pair_row(unsigned char* stage, uint64_t* bar, const float* fin0, const SM* finm,
-                                            const float* kappa, int plane, int pitch, int nx, int ny, int row,
-                                            int a0, int a1, int b0, int bm, uint32_t bytes)
-{
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) mbar_arrive_tx(bar, bytes);
-    __syncwarp();
-    const int np = kappa ? 10 : 9;
-    if (lane < np) {
-        // c_ly of population l: 0 0 1 1 1 0 -1 -1 -1 (kappa: its own row)
-        const int cy = (lane >= 2 && lane <= 4) ? 1 : ((lane >= 6 && lane <= 8) ? -1 : 0);
-        int r = row - cy;
-        r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-        const char* src;
-        int es;
-        unsigned char* dst;
-        if (lane == 0) {
-            src = reinterpret_cast<const char*>(fin0 + (long long)r * pitch);
-            es = 4;
-            dst = stage;
-        } else if (lane < 9) {
-            src = reinterpret_cast<const char*>(finm + ((long long)(lane - 1) * plane + (long long)r * pitch));
-            es = (int)sizeof(SM);
-            dst = stage + b0 + (lane - 1) * bm;
-        } else {
-            src = reinterpret_cast<const char*>(kappa + (long long)r * nx);
-            es = 4;
-            dst = stage + b0 + 8 * bm;
-        }
-        int c = a0;
-        if (c < 0) {  // left periodic image
-            bulk_g2s(dst, src + (long long)(c + nx) * es, (uint32_t)(-c * es), bar);
-            dst += -c * es;
-            c = 0;
-        }
-        const int e = a1 < nx ? a1 : nx;
-        bulk_g2s(dst, src + (long long)c * es, (uint32_t)((e - c) * es), bar);
-        dst += (e - c) * es;
-        if (a1 > nx) bulk_g2s(dst, src, (uint32_t)((a1 - nx) * es), bar);  // right image
-    }
-}
-
-// ---------------------------------------------------------------------------
 // One CTA of BX threads covers NC = 2 BX consecutive columns x0-2 .. x0+NC-3
 // (thread t: local columns j = 2t, 2t+1) and marches down a band of rows;
 // neighbouring CTAs overlap by 4 columns and each stores NC - 4.  The march
 // is step_band's: step k forms h of row r(k) into a 4-row shared ring, one
 // barrier, then the pressure of row r(k-1) and force, collision and store of
-// row r(k-3).  The pulled values of row r(k) come either from registers
-// loaded one row ahead plus warp shuffles (TMA = false), or from a shared
-// stage filled by bulk copies kPairStages rows ahead (TMA = true).
-template <typename SM, int BX, bool OMEGA1, bool KFIELD, bool TMA>
+// row r(k-3).  The pulled values of row r(k) come from registers loaded
+// one or two rows ahead, plus warp shuffles for the values that cross a pair
+// boundary.
+template <typename SM, int BX, bool OMEGA1, bool KFIELD>
 __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const SM* __restrict__ finm,
                                            float* __restrict__ fout0, SM* __restrict__ foutm,
                                            const float* __restrict__ kappa, const Geom& G,
-                                           const Consts<float>& C, int strip, int band, int nbands,
-                                           unsigned char* stage_mem)
+                                           const Consts<float>& C, int strip, int band, int nbands)
 {
     using IO = PairIO<SM>;
     using V = typename IO::V;
-    using L = PairStage<SM, BX, KFIELD>;
+    constexpr bool NARROW = !std::is_same<SM, float>::value;
     constexpr int NC = 2 * BX;  // columns per CTA
     constexpr int W = NC - 4;   // output columns per CTA
     constexpr int OFF = 2;      // ring slot of local column j is OFF + j (keeps pairs 8-byte aligned)
@@ -341,13 +273,14 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     __shared__ __align__(16) float psm[4][NC + 4];  // film pressure
     // general tau: the eight pulled moving populations of the last four rows
     __shared__ __align__(16) float2 fsm[OMEGA1 ? 1 : 4][8][OMEGA1 ? 1 : BX];
-    __shared__ __align__(8) uint64_t bars[TMA ? kPairStages : 1];
+    // per-thread ring of j_x, j_y, the pull-sum residual and 1/h of the last
+    // four rows (each thread reads back only its own slots)
+    __shared__ __align__(16) float2 rsm[4][4][BX];
 
     const int t = threadIdx.x, lane = t & 31;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
     const int x0 = strip * W;
     const int weff = min(W, nx - x0);     // output columns of this CTA (even)
-    const bool hcol = 2 * t <= weff + 3;  // h needed at local columns 0 .. weff+3
     const bool pcol = 2 * t <= weff + 2;  // p needed at local columns 1 .. weff+2
     const bool ocol = t >= 1 && 2 * t <= weff;
     const int ybeg = (int)(((long long)band * ny) / nbands);
@@ -359,7 +292,6 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     const float Rax = C.r_axis, Rdg = C.r_diag;
     const int c = wrap_index(x0 - 2 + 2 * t, nx);  // own pair (even)
 
-    // ---- per-thread loads: registers of the row in flight
     const bool edge = lane == 0 || lane == 31;
     const int ce = lane == 0 ? wrap_index(c - 2, nx) : (c + 2 == nx ? 0 : c + 2);
     // moving planes (index l - 1) a warp-edge lane reads at its outer
@@ -371,62 +303,44 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     const float2* __restrict__ f0p = reinterpret_cast<const float2*>(fin0);
     const V* __restrict__ fmp = reinterpret_cast<const V*>(finm);
     const int half = plane >> 1;  // pairs per plane (pitch is even)
-    float2 q0;
-    V qm[8], qe[3];
-
-    // ---- bulk copies: the row segment [a0, a1) per plane; column X at X - a0
-    const int a0 = floor_div(x0 - 4, L::A) * L::A;
-    const int a1 = (x0 + weff + 4 + L::A - 1) / L::A * L::A;
-    const int col = x0 - 2 + 2 * t - a0;
-    const uint32_t bytes_step = (uint32_t)(a1 - a0) * (uint32_t)(4 + 8 * sizeof(SM) + (KFIELD ? 4 : 0));
-    auto issue = [&](int j) {  // march step j (h row r(j)) into stage j % kPairStages
-        const int st = j & (kPairStages - 1);
-        issue_pair_row<SM>(stage_mem + st * L::STAGE, &bars[st], fin0, finm, KFIELD ? kappa : nullptr, plane,
-                           pitch, nx, ny, wrap_index(rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step);
-    };
-    bool gave_up = false;  // this thread stopped waiting for a stage (TMA)
+    // PF rows of loads in flight: 16-bit storage keeps two (rows r(k+1) and
+    // r(k+2) go out while step k runs), FP32 one (its registers would
+    // otherwise cost resident warps)
+    constexpr int PF = NARROW ? 2 : 1;
+    float2 q0[PF];
+    V qm[PF][8], qe[PF][3];
 
     // wrapped rows r(k-1), r(k), r(k+1), r(k+2)
+    // wrapped rows r(k-1) .. r(k+3)
     int wm1 = wrap_index(rstart - dir, ny), w0 = wrap_index(rstart, ny);
     int w1 = wrap_index(rstart + dir, ny), w2 = wrap_index(rstart + 2 * dir, ny);
-    auto load_row = [&](int wb, int w, int wa) {
+    int w3 = wrap_index(rstart + 3 * dir, ny);
+    // the nine planes (and the edge planes) pulled into row w, into register set b
+    auto load_row = [&](auto b_c, int wb, int w, int wa) {
+        constexpr int b = decltype(b_c)::value;
         const int ys = dir > 0 ? wb : wa, yn = dir > 0 ? wa : wb;  // rows y-1, y+1
         const int i0 = (w * pitch + c) >> 1, is = (ys * pitch + c) >> 1, in = (yn * pitch + c) >> 1;
-        q0 = ldpair(f0p + i0);
-        qm[0] = ldpair(fmp + i0);               // l = 1 from row y
-        qm[1] = ldpair(fmp + (half + is));      // l = 2 from row y-1
-        qm[2] = ldpair(fmp + (2 * half + is));  // l = 3
-        qm[3] = ldpair(fmp + (3 * half + is));  // l = 4
-        qm[4] = ldpair(fmp + (4 * half + i0));  // l = 5 from row y
-        qm[5] = ldpair(fmp + (5 * half + in));  // l = 6 from row y+1
-        qm[6] = ldpair(fmp + (6 * half + in));  // l = 7
-        qm[7] = ldpair(fmp + (7 * half + in));  // l = 8
+        q0[b] = ldpair(f0p + i0);
+        qm[b][0] = ldpair(fmp + i0);               // l = 1 from row y
+        qm[b][1] = ldpair(fmp + (half + is));      // l = 2 from row y-1
+        qm[b][2] = ldpair(fmp + (2 * half + is));  // l = 3
+        qm[b][3] = ldpair(fmp + (3 * half + is));  // l = 4
+        qm[b][4] = ldpair(fmp + (4 * half + i0));  // l = 5 from row y
+        qm[b][5] = ldpair(fmp + (5 * half + in));  // l = 6 from row y+1
+        qm[b][6] = ldpair(fmp + (6 * half + in));  // l = 7
+        qm[b][7] = ldpair(fmp + (7 * half + in));  // l = 8
         if (edge) {
-            qe[0] = ldpair(fmp + ((e0 + w * pitch + ce) >> 1));
-            qe[1] = ldpair(fmp + ((e1 + ys * pitch + ce) >> 1));
-            qe[2] = ldpair(fmp + ((e2 + yn * pitch + ce) >> 1));
+            qe[b][0] = ldpair(fmp + ((e0 + w * pitch + ce) >> 1));
+            qe[b][1] = ldpair(fmp + ((e1 + ys * pitch + ce) >> 1));
+            qe[b][2] = ldpair(fmp + ((e2 + yn * pitch + ce) >> 1));
         }
     };
 
     float2 kap_n = pk(C.kappa_u);
-    if constexpr (TMA) {
-        if (t == 0) {
-#pragma unroll
-            for (int s = 0; s < kPairStages; ++s) mbar_init(&bars[s], 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
-        if (t < 32)
-            for (int j = 0; j < kPairStages && j <= R + 3; ++j) issue(j);
-        if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
-    } else {
-        load_row(wm1, w0, w1);
-        if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
-    }
+    load_row(std::integral_constant<int, 0>{}, wm1, w0, w1);
+    if constexpr (PF == 2) load_row(std::integral_constant<int, 1>{}, w0, w1, w2);
+    if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
 
-    float2 jxv[4], jyv[4], ihv[4], erv[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) jxv[s] = jyv[s] = ihv[s] = erv[s] = pk(0.0f);
     // ring slots no thread writes (outer halves of the edge columns' stencils)
     if (t < 4) {
         const int j = t < 2 ? t : NC + t;
@@ -434,8 +348,7 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         for (int s = 0; s < 4; ++s) hsm[s][j] = psm[s][j] = 0.0f;
     }
 
-    // one march step; false when the CTA gave up waiting for a bulk copy
-    auto body = [&](auto stage_c, int k) -> bool {
+    auto body = [&](auto stage_c, int k) {
         constexpr int s = decltype(stage_c)::value;  // ring slot of row r(k)
         constexpr int s1 = (s + 3) & 3;              // r(k-1)
         constexpr int s2 = (s + 2) & 3;              // r(k-2)
@@ -444,64 +357,27 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         // ---- (A) h, j of row r(k)
         if (k <= R + 3) {
             float2 f0, n[8];  // f_0 - href and the moving populations arriving at the pair
-            bool have = true;
-            if constexpr (TMA) {
-                have = hcol;
-                if (hcol) {
-                    const uint32_t parity = (uint32_t)(k / kPairStages) & 1u;
-                    if (C.wait_limit <= 0) {
-                        have = false;
-                    } else {
-                        int it = 0;
-                        while (!mbar_test(&bars[s], parity)) {
-                            if (++it >= C.wait_limit) {
-                                have = false;
-                                break;
-                            }
-                        }
-                    }
-                    gave_up = !have;
-                }
-                if (have) {
-                    const unsigned char* base = stage_mem + s * L::STAGE;
-                    const float* p0 = reinterpret_cast<const float*>(base);
-                    const SM* pm = reinterpret_cast<const SM*>(base + L::B0);
-                    constexpr int M = L::LMAX;
-                    auto own = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col),
-                                                                   (m & 1) ? Rdg : Rax, C); };
-                    auto left = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col - 2),
-                                                                    (m & 1) ? Rdg : Rax, C).y; };
-                    auto right = [&](int m) { return decode_pair<SM>(*reinterpret_cast<const V*>(pm + m * M + col + 2),
-                                                                     (m & 1) ? Rdg : Rax, C).x; };
-                    f0 = *reinterpret_cast<const float2*>(p0 + col);
-                    const float2 o1 = own(0), o2 = own(1), o4 = own(3), o5 = own(4), o6 = own(5), o8 = own(7);
-                    n[0] = make_float2(left(0), o1.x);
-                    n[1] = make_float2(left(1), o2.x);
-                    n[2] = own(2);
-                    n[3] = make_float2(o4.y, right(3));
-                    n[4] = make_float2(o5.y, right(4));
-                    n[5] = make_float2(o6.y, right(5));
-                    n[6] = own(6);
-                    n[7] = make_float2(left(7), o8.x);
-                    if (KFIELD && pcol)
-                        kap_n = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base + L::B0 + 8 * L::BM) + col);
-                }
-            } else {
-                f0 = q0;
+            {
+                constexpr int rb = s % PF;  // register set of row r(k)
+                f0 = q0[rb];
                 float2 v[8];
 #pragma unroll
-                for (int l = 0; l < 8; ++l) v[l] = decode_pair<SM>(qm[l], (l & 1) ? Rdg : Rax, C);
+                for (int l = 0; l < 8; ++l) v[l] = decode_pair<SM>(qm[rb][l], (l & 1) ? Rdg : Rax, C);
                 float ex = 0.f, ey = 0.f, ez = 0.f;  // left column of lane 0 / right column of lane 31
                 if (edge) {
-                    const float2 a = decode_pair<SM>(qe[0], Rax, C);  // l = 1 or 5: axis
-                    const float2 b = decode_pair<SM>(qe[1], Rdg, C);  // l = 2 or 4: diagonal
-                    const float2 d = decode_pair<SM>(qe[2], Rdg, C);  // l = 8 or 6: diagonal
+                    const float2 a = decode_pair<SM>(qe[rb][0], Rax, C);  // l = 1 or 5: axis
+                    const float2 b = decode_pair<SM>(qe[rb][1], Rdg, C);  // l = 2 or 4: diagonal
+                    const float2 d = decode_pair<SM>(qe[rb][2], Rdg, C);  // l = 8 or 6: diagonal
                     ex = lane == 0 ? a.y : a.x;
                     ey = lane == 0 ? b.y : b.x;
                     ez = lane == 0 ? d.y : d.x;
                 }
-                // the loads of row r(k+1) go out before this row's arithmetic
-                if (k + 1 <= R + 3) load_row(w0, w1, w2);
+                // the loads of row r(k+PF) go out before this row's arithmetic
+                if constexpr (PF == 2) {
+                    if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
+                } else {
+                    if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
+                }
                 if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)w0 * nx + c));
                 // l = 1, 2, 8 arrive from the left, l = 4, 5, 6 from the right
                 float u1 = __shfl_up_sync(0xffffffffu, v[0].y, 1);
@@ -521,32 +397,24 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 n[6] = v[6];
                 n[7] = make_float2(u8, v[7].x);
             }
-            if (have) {
-                float2 dh, er, jx, jy;
-                pair_moments(n, f0, dh, er, jx, jy);
-                *reinterpret_cast<float2*>(&hsm[s][OFF + 2 * t]) = dh;
-                erv[s] = er;
-                jxv[s] = jx;
-                jyv[s] = jy;
-                if constexpr (!OMEGA1) {
+            float2 dh, er, jx, jy;
+            pair_moments(n, f0, dh, er, jx, jy);
+            *reinterpret_cast<float2*>(&hsm[s][OFF + 2 * t]) = dh;
+            rsm[s][0][t] = jx;
+            rsm[s][1][t] = jy;
+            rsm[s][2][t] = er;
+            if constexpr (!OMEGA1) {
 #pragma unroll
-                    for (int l = 0; l < 8; ++l) fsm[s][l][t] = n[l];
-                }
+                for (int l = 0; l < 8; ++l) fsm[s][l][t] = n[l];
             }
         }
-        if constexpr (TMA) {
-            // every thread is done with this stage (or the CTA gives up)
-            if (__syncthreads_or(gave_up)) return false;
-            if (t < 32 && k + kPairStages <= R + 3) issue(k + kPairStages);
-        } else {
-            __syncthreads();
-        }
+        __syncthreads();
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
         if (pcol && k >= 2 && k <= R + 3) {
             float2 ih;
             const float2 p = pair_pressure(hsm[s] + OFF + 2 * t, hsm[s1] + OFF + 2 * t, hsm[s2] + OFF + 2 * t, kap,
                                            disj, C, ih);
-            ihv[s1] = ih;
+            rsm[s1][3][t] = ih;
             *reinterpret_cast<float2*>(&psm[s1][OFF + 2 * t]) = p;
         }
         // ---- (B2) force, collision and store of row r(k-3)
@@ -558,143 +426,96 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
             const float2 dh = *reinterpret_cast<const float2*>(&hsm[s3][OFF + 2 * t]);
             const float2* fp = nullptr;
             if constexpr (!OMEGA1) fp = &fsm[s3][0][t];
-            pair_collide_store<SM, OMEGA1>(pn, pc, ps, dh, ihv[s3], jxv[s3], jyv[s3], erv[s3], fp, BX, fout0,
+            pair_collide_store<SM, OMEGA1>(pn, pc, ps, dh, rsm[s3][3][t], rsm[s3][0][t], rsm[s3][1][t], rsm[s3][2][t], fp, BX, fout0,
                                            foutm, o * pitch + c, plane, C);
         }
         wm1 = w0;
         w0 = w1;
         w1 = w2;
-        w2 += dir;
-        w2 = w2 == ny ? 0 : (w2 < 0 ? ny - 1 : w2);
-        return true;
+        w2 = w3;
+        w3 += dir;
+        w3 = w3 == ny ? 0 : (w3 < 0 ? ny - 1 : w3);
     };
 
     const int last = R + 4;
-    int k = 0;
-    bool ok = true;
-    for (;;) {
-        if (!(ok = body(std::integral_constant<int, 0>{}, k))) break;
+    for (int k = 0;;) {
+        body(std::integral_constant<int, 0>{}, k);
         if (++k > last) break;
-        if (!(ok = body(std::integral_constant<int, 1>{}, k))) break;
+        body(std::integral_constant<int, 1>{}, k);
         if (++k > last) break;
-        if (!(ok = body(std::integral_constant<int, 2>{}, k))) break;
+        body(std::integral_constant<int, 2>{}, k);
         if (++k > last) break;
-        if (!(ok = body(std::integral_constant<int, 3>{}, k))) break;
+        body(std::integral_constant<int, 3>{}, k);
         if (++k > last) break;
-    }
-    if constexpr (TMA) {
-        if (!ok && t == 0) {
-            // report, then wait (bounded) for the copies still in flight
-            // before the CTA's shared memory is released: the last march step
-            // issued is jmax; stage s holds at most one unfinished phase, its
-            // last issued step
-            if (C.status) atomicOr(C.status, kStatusTimeout);
-            const int jmax = min(k + kPairStages - 1, R + 3);
-            for (int s = 0; s < kPairStages; ++s) {
-                if (jmax < s) continue;
-                const int jl = jmax - ((jmax - s) % kPairStages);
-                int it = 0;
-                while (!mbar_test(&bars[s], (uint32_t)(jl / kPairStages) & 1u) && ++it < kWaitLimit) {
-                }
-            }
-        }
     }
 }
 
+// Register budget: 80 per thread (24 resident warps per SM), at which the
+// kernel does not spill (measured faster than 128 registers and 16 warps).
 template <typename SM, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX, 512 / BX)
+__global__ void __launch_bounds__(BX, 768 / BX)
 k_step2(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __restrict__ fout0,
         SM* __restrict__ foutm, const float* __restrict__ kappa, const Geom G, const Consts<float> C)
 {
-    step_band2<SM, BX, OMEGA1, KFIELD, false>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
-                                              gridDim.y, nullptr);
-}
-
-template <typename SM, int BX, bool OMEGA1, bool KFIELD>
-__global__ void __launch_bounds__(BX, 512 / BX)
-k_step2_tma(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __restrict__ fout0,
-            SM* __restrict__ foutm, const float* __restrict__ kappa, const Geom G, const Consts<float> C)
-{
-    extern __shared__ __align__(128) unsigned char pair_stage_mem[];
-    step_band2<SM, BX, OMEGA1, KFIELD, true>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y,
-                                             gridDim.y, pair_stage_mem);
+    dependent_launch_entry();
+    step_band2<SM, BX, OMEGA1, KFIELD>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y, gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
-// Launch of the paired kernels: block_x is the CTA width in columns (64, 128
+// Launch of the paired kernel: block_x is the CTA width in columns (64, 128
 // or 256), i.e. block_x / 2 threads.
 
-template <typename SM, int BX, bool OM1, bool KF>
-cudaError_t pair_one(bool tma, dim3 grid, const float* fin0, const SM* finm, float* fout0, SM* foutm,
-                     const float* kappa, const Geom& G, const Consts<float>& C, cudaStream_t st)
-{
-    if (tma) {
-        using L = PairStage<SM, BX, KF>;
-        static bool attr = false;  // one attribute call per instantiation
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_step2_tma<SM, BX, OM1, KF>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        k_step2_tma<SM, BX, OM1, KF><<<grid, BX, L::BYTES, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-    } else {
-        k_step2<SM, BX, OM1, KF><<<grid, BX, 0, st>>>(fin0, finm, fout0, foutm, kappa, G, C);
-    }
-    return cudaGetLastError();
-}
-
 template <typename SM, int BX>
-cudaError_t launch_pair_bx(bool tma, const float* fin0, const SM* finm, float* fout0, SM* foutm,
-                           const float* kappa, const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
+cudaError_t launch_pair_bx(const float* fin0, const SM* finm, float* fout0, SM* foutm, const float* kappa,
+                           const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
 {
     int bands = (G.ny + rows - 1) / rows;
     if (bands > 65535) bands = 65535;
     constexpr int W = 2 * BX - 4;
-    dim3 grid((G.nx + W - 1) / W, bands);
+    const dim3 grid((G.nx + W - 1) / W, bands);
     const bool om1 = C.omega == 1.0f;
     if (kappa) {
-        if (om1) return pair_one<SM, BX, true, true>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
-        return pair_one<SM, BX, false, true>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+        if (om1) return launch_dependent(k_step2<SM, BX, true, true>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
+        return launch_dependent(k_step2<SM, BX, false, true>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
     }
-    if (om1) return pair_one<SM, BX, true, false>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
-    return pair_one<SM, BX, false, false>(tma, grid, fin0, finm, fout0, foutm, kappa, G, C, st);
+    if (om1) return launch_dependent(k_step2<SM, BX, true, false>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
+    return launch_dependent(k_step2<SM, BX, false, false>, grid, BX, 0, st, fin0, finm, fout0, foutm, kappa, G, C);
 }
 
-template <typename SM>
-cudaError_t launch_pair(bool tma, int block_x, const float* fin0, const SM* finm, float* fout0, SM* foutm,
-                        const float* kappa, const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
+template <typename SM, int BX, bool OM1, bool KF>
+int bps_pair_one()
 {
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<SM, BX, OM1, KF>, BX, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+// The paired step for one storage type.
+template <typename SM>
+cudaError_t pair_step(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
+                      const Consts<float>& C, int rows, cudaStream_t st)
+{
+    const float* f0 = (const float*)fin;
+    const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(float));
+    float* g0 = (float*)fout;
+    SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
+    const float* k = (const float*)kappa;
     switch (block_x) {
-        case 64: return launch_pair_bx<SM, 32>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
-        case 128: return launch_pair_bx<SM, 64>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
-        case 256: return launch_pair_bx<SM, 128>(tma, fin0, finm, fout0, foutm, kappa, G, C, rows, st);
+        case 64: return launch_pair_bx<SM, 32>(f0, fm, g0, gm, k, G, C, rows, st);
+        case 128: return launch_pair_bx<SM, 64>(f0, fm, g0, gm, k, G, C, rows, st);
+        case 256: return launch_pair_bx<SM, 128>(f0, fm, g0, gm, k, G, C, rows, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename SM, int BX, bool OM1, bool KF>
-int bps_pair_one(bool tma)
-{
-    int n = 0;
-    cudaError_t e;
-    if (tma) {
-        using L = PairStage<SM, BX, KF>;
-        cudaFuncSetAttribute(k_step2_tma<SM, BX, OM1, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_tma<SM, BX, OM1, KF>, BX, L::BYTES);
-    } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<SM, BX, OM1, KF>, BX, 0);
-    }
-    return e == cudaSuccess ? n : 0;
-}
-
+// Resident CTAs per SM of the paired step for a CTA width (0 if unknown).
 template <typename SM>
-int blocks_per_sm_pair(bool tma, int block_x, bool omega1, bool kfield)
+int pair_blocks_per_sm(int block_x, bool omega1, bool kfield)
 {
     auto pick = [&](auto bx_c) {
         constexpr int BX = decltype(bx_c)::value;
-        if (kfield) return omega1 ? bps_pair_one<SM, BX, true, true>(tma) : bps_pair_one<SM, BX, false, true>(tma);
-        return omega1 ? bps_pair_one<SM, BX, true, false>(tma) : bps_pair_one<SM, BX, false, false>(tma);
+        if (kfield) return omega1 ? bps_pair_one<SM, BX, true, true>() : bps_pair_one<SM, BX, false, true>();
+        return omega1 ? bps_pair_one<SM, BX, true, false>() : bps_pair_one<SM, BX, false, false>();
     };
     switch (block_x) {
         case 64: return pick(std::integral_constant<int, 32>{});

@@ -4,7 +4,8 @@ Two independent predictions of how a small sinusoidal perturbation
 h = h0 + eps cos(k x) of a flat film evolves:
 
 * ``scheme_growth_rate``: the exact linearisation of one step of the lattice
-  Boltzmann scheme of Section II (Eq. LBE with the equilibria, the force of
+  Boltzmann scheme of Section II (and of the labelled second-order-forcing
+  alternative, ``forcing=1``) (Eq. LBE with the equilibria, the force of
   Eq. force and the stencils of Eqs. derivative / n_laplace) for a mode that
   is uniform in y.  Grouping the nine populations by c_x in {-1, 0, +1} makes
   the linearised step a 3 x 3 matrix; its dominant eigenvalue mu gives the
@@ -50,7 +51,11 @@ def pressure_symbol(k, gamma, kap=0.0, fprime=0.0, pi_sign=1):
     return 2.0 * gamma * (1.0 - math.cos(k)) - pi_sign * gamma * kap * fprime
 
 
-def scheme_growth_rate(k, h0, g, gamma, tau, delta, kap=0.0, fprime=0.0, pi_sign=1):
+def scheme_growth_rate(k, h0, g, gamma, tau, delta, kap=0.0, fprime=0.0, pi_sign=1, forcing=0):
+    """forcing = 0: Eq. (LBE) as printed, u' = q'/h0 and the source 3 w_l c_l.F.
+    forcing = 1: the second-order alternative, h0 u' = (q' + F_ext'/2) /
+    (1 + lambda/2) (the friction -lambda h0 u' taken at that velocity) and
+    the source scaled by (1 - omega/2) (its u.F terms are second order)."""
     omega = 1.0 / tau
     nu = (tau - 0.5) / 3.0
     lam = nu * alpha(h0, delta) / h0
@@ -59,11 +64,18 @@ def scheme_growth_rate(k, h0, g, gamma, tau, delta, kap=0.0, fprime=0.0, pi_sign
     # order: (A-, A0, A+);  h' = A- + A0 + A+,  q' = A+ - A-
     Hrow = np.array([1.0, 1.0, 1.0], complex)
     Qrow = np.array([-1.0, 0.0, 1.0], complex)
-    Eq = np.array([g * h0 / 2.0 * Hrow - 0.5 * Qrow,
+    Fext = -1j * h0 * s * P * Hrow          # film-pressure force, linearised
+    if forcing == 0:
+        Urow = Qrow                          # h0 u'
+        scale = 1.0
+    else:
+        Urow = (Qrow + 0.5 * Fext) / (1.0 + 0.5 * lam)
+        scale = 1.0 - 0.5 * omega
+    Eq = np.array([g * h0 / 2.0 * Hrow - 0.5 * Urow,
                    (1.0 - g * h0) * Hrow,
-                   g * h0 / 2.0 * Hrow + 0.5 * Qrow])
-    Frow = -lam * Qrow - 1j * h0 * s * P * Hrow
-    Src = np.array([-0.5 * Frow, 0.0 * Frow, 0.5 * Frow])
+                   g * h0 / 2.0 * Hrow + 0.5 * Urow])
+    Frow = -lam * Urow + Fext
+    Src = scale * np.array([-0.5 * Frow, 0.0 * Frow, 0.5 * Frow])
     post = (1.0 - omega) * np.eye(3) + omega * Eq + Src
     stream = np.diag([np.exp(1j * k), 1.0, np.exp(-1j * k)])
     mu = np.linalg.eigvals(stream @ post)

@@ -378,42 +378,45 @@ def test_parity_async_copy_pipeline(dtype, nx, ny, rows):
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("pipeline", [3, 4])
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("tau", [1.0, 0.75])
+@pytest.mark.parametrize("theta_field", [True, False])
 @pytest.mark.parametrize("nx,ny,block_x", [(16, 9, 64), (64, 48, 64), (200, 33, 128), (304, 41, 256),
-                                           (520, 70, 128), (2, 5, 64)])
-def test_parity_paired_pipelines(pipeline, dtype, tau, nx, ny, block_x):
-    """The two-column kernels (3: per-thread loads and lane shuffles; 4:
-    rows staged by bulk copies) against the oracle, at both relaxation
-    kernels, every storage type they take and CTA widths of 64, 128 and 256
-    columns, including lattices narrower than one CTA (strips wrap on both
-    sides) and several strips with a ragged last one."""
-    if pipeline == 4 and nx % 8:
-        pytest.skip("bulk copies need nx a multiple of 8")
+                                           (520, 70, 128), (2, 5, 64), (6, 1, 128)])
+def test_parity_two_column_pipeline(dtype, tau, theta_field, nx, ny, block_x):
+    """The two-column kernel (pipeline 3: aligned pair loads, lane shuffles
+    for the values that cross a pair boundary) against the oracle, at both
+    relaxation kernels, with and without a theta field, every storage type it
+    takes and CTA widths of 64, 128 and 256 columns, including lattices
+    narrower than one CTA (strips wrap on both sides), one row, and several
+    strips with a ragged last one."""
     h0, th, p = inputs.small_random(nx, ny, seed=nx * 11 + ny, amp=0.05)
     p.update(tau=tau, g=2e-4, gx_body=2e-5, gy_body=-1e-5, delta=1.0)
-    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=pipeline, block_x=block_x, rows=7))
+    r = run_both(h0, th, p, 100, dtype, launch=dict(pipeline=3, block_x=block_x, rows=7),
+                 theta_uniform=None if theta_field else math.radians(20.0))
     assert rel_linf(r["h"], r["ho"]) <= TOL[dtype]
     assert abs(r["gm1"] - r["gm0"]) <= 1e-6 * r["gm0"]
 
 
-def test_paired_pipelines_agree_bitwise():
-    """Both two-column kernels compute every node with the same operations
-    in the same order (they differ only in how the pulled values reach the
-    thread), so their states are identical bit for bit."""
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_two_column_band_heights_agree_bitwise(dtype):
+    """With the same CTA width, every node of the two-column kernel runs the
+    same instruction sequence whatever the band height or graph chunking, so
+    the states are identical bit for bit."""
     h0, th, p = inputs.small_random(304, 141, seed=19, amp=0.05)
     p.update(tau=0.9, gx_body=1e-5)
     states = []
-    for pipe in (3, 4):
-        sim = ThinFilm(p, h0, th)
-        sim.set_launch(pipeline=pipe, block_x=128, rows=13, graph_chunk=0)
+    for rows, chunk in ((13, 0), (1, 0), (64, 4), (141, 0)):
+        sim = ThinFilm(p, h0, th, dtype=dtype)
+        sim.set_launch(pipeline=3, block_x=128, rows=rows, graph_chunk=chunk)
         sim.step(25)
         states.append(sim.get_state())
-    assert torch.equal(states[0], states[1])
+        sim.close()
+    for st in states[1:]:
+        assert torch.equal(states[0], st)
 
 
-@pytest.mark.parametrize("pipeline,dtype", [(0, "f32"), (0, "f16"), (4, "f32"), (4, "bf16")])
+@pytest.mark.parametrize("pipeline,dtype", [(0, "f32"), (0, "f16"), (0, "bf16"), (0, "f64")])
 def test_bulk_copy_wait_limit_reports_timeout(pipeline, dtype):
     """A bulk-copy step kernel that gives up waiting for its own row copies
     sets TF_LBM_STATUS_TIMEOUT, stops issuing, waits (bounded) for the copies

@@ -151,6 +151,54 @@ def test_alpha_no_slip_limit():
         assert O.alpha(h, 1.0) < O.alpha(h, 0.5) < O.alpha(h, 0.0)
 
 
+def _navier_slip_mobility(h, delta):
+    """Volume flux per unit pressure gradient (mu = 1) of a film of height h
+    on a substrate with Navier slip length delta: solve u'' = -1 on
+    [0, h] with u(0) = delta u'(0) and a stress-free surface u'(h) = 0 by
+    finite differences, and integrate u over the height."""
+    n = 2001
+    z = np.linspace(0.0, h, n)
+    dz = z[1] - z[0]
+    A = np.zeros((n, n))
+    b = np.full(n, -dz * dz)
+    for i in range(1, n - 1):
+        A[i, i - 1], A[i, i], A[i, i + 1] = 1.0, -2.0, 1.0
+    # u0 - delta (-3 u0 + 4 u1 - u2) / (2 dz) = 0 (second-order one-sided)
+    A[0, 0], A[0, 1], A[0, 2] = 1.0 + 3.0 * delta / (2 * dz), -4.0 * delta / (2 * dz), delta / (2 * dz)
+    b[0] = 0.0
+    # (3 u_n - 4 u_{n-1} + u_{n-2}) / (2 dz) = 0
+    A[-1, -1], A[-1, -2], A[-1, -3] = 3.0, -4.0, 1.0
+    b[-1] = 0.0
+    u = np.linalg.solve(A, b)
+    return float(np.sum((u[1:] + u[:-1]) * 0.5) * dz)
+
+
+@pytest.mark.parametrize("h", [0.07, 0.4, 1.0, 3.0])
+def test_alpha_slip_expansion_against_navier_slip_mobility(h):
+    """Eq. (alphafric) at delta > 0.  In the friction-dominated balance
+    -h grad p = nu alpha u the film carries the flux h u = -(h^2 / alpha)
+    grad p / mu, so h^2 / alpha_delta is the model's mobility.  Its terms of
+    order 1 and delta must be the Navier-slip lubrication mobility
+    h^3/3 + delta h^2, computed here from the slip Poiseuille profile (no
+    formula of the model involved); the remainder is exactly the printed
+    quadratic regularisation delta^2 h / 2 (a polynomial in delta of degree
+    two: a mis-typed coefficient, e.g. delta^2 for 3 delta^2 in the
+    denominator, fails the first or the second check)."""
+    mob = lambda d: h * h / O.alpha(h, d)
+    for delta in (0.05, 0.2, 0.7):
+        navier = _navier_slip_mobility(h, delta)
+        assert abs(navier - (h ** 3 / 3 + delta * h * h)) <= 1e-5 * navier
+        # the part of h^2/alpha beyond the Navier mobility, divided by delta^2
+        rest = (mob(delta) - navier) / (delta * delta)
+        assert abs(rest - h / 2) <= 1e-4 * (h / 2) + 1e-5 * navier / (delta * delta)
+    # the slope in delta at 0 is the slip term h^2 and the curvature is h
+    d = 1e-3
+    slope = (mob(d) - mob(-d)) / (2 * d)
+    curv = (mob(d) - 2 * mob(0.0) + mob(-d)) / (d * d)
+    assert abs(slope - h * h) <= 1e-8 * max(1.0, h * h)
+    assert abs(curv - h) <= 1e-5 * max(1.0, h)
+
+
 # ------------------------------------------------ whole-step invariants
 
 def test_flat_film_stays_flat():
@@ -199,6 +247,45 @@ def test_uniform_film_body_force_closed_form(tau, delta):
             assert np.allclose(u, expect, rtol=1e-11, atol=1e-18)
 
 
+@pytest.mark.parametrize("tau,delta", [(1.0, 0.0), (0.9, 0.5), (1.3, 2.0)])
+def test_second_order_forcing_uniform_film_closed_form(tau, delta):
+    """The labelled second-order-forcing alternative (forcing = 1) on a
+    uniform film under F = h g_par: momentum gains exactly F per step, and
+    with u = (j + F/2)/h and the friction -lambda h u taken at that velocity
+    j_{n+1} = r j_n + h g_par / (1 + lambda/2), r = (1 - lambda/2)/(1 + lambda/2),
+    lambda = nu alpha / h, so j_n = (h g_par / lambda)(1 - r^n): the same
+    terminal velocity as the printed scheme, approached without the sign
+    alternation of the explicit friction at lambda > 1."""
+    hh, gx, gy = 1.5, 1e-5, -2e-5
+    cfg = O.Config(nx=6, ny=5, tau=tau, delta=delta, gx_body=gx, gy_body=gy, g=2e-4, forcing=1)
+    f = O.init(cfg, np.full((5, 6), hh))
+    kap = O.kappa_field(cfg, math.radians(30))
+    nu = (tau - 0.5) / 3
+    lam = nu * LT.alpha(hh, delta) / hh
+    r = (1 - lam / 2) / (1 + lam / 2)
+    for nstep in range(1, 61):
+        O.step(cfg, kap, f, 1)
+        _, ux, uy = O.moments(cfg, f)
+        for g_, u in ((gx, ux), (gy, uy)):
+            expect = g_ / lam * (1 - r ** nstep)
+            assert np.allclose(u, expect, rtol=1e-11, atol=1e-18)
+
+
+def test_second_order_forcing_conserves_mass_and_flat_film():
+    h0, th, p = inputs.small_random(40, 36, seed=5, amp=0.2)
+    cfg = cfg_of(p, tau=0.9, gx_body=1e-5, gy_body=-3e-6, g=1e-4, forcing=1)
+    kap = O.kappa_field(cfg, th)
+    f = O.init(cfg, h0)
+    m0 = O.mass(cfg, f)
+    O.step(cfg, kap, f, 300)
+    assert abs(O.mass(cfg, f) - m0) < 1e-13 * m0
+    cfg = O.Config(nx=12, ny=10, tau=0.8, g=-1e-4, delta=1.0, forcing=1)
+    f = O.init(cfg, np.full((10, 12), 1.3))
+    O.step(cfg, O.kappa_field(cfg, math.radians(25)), f, 200)
+    h, ux, uy = O.moments(cfg, f)
+    assert np.ptp(h) == 0 and np.abs(ux).max() < 1e-14
+
+
 # ------------------------------------------- linear stability (RT, Pi)
 
 def _mode_growth(cfg, kap, h0, k, steps, every, skip):
@@ -217,18 +304,75 @@ def _mode_growth(cfg, kap, h0, k, steps, every, skip):
     return np.polyfit(ts[sel], la[sel], 1)[0]
 
 
+@pytest.mark.parametrize("forcing", [0, 1])
 @pytest.mark.parametrize("mode,tau,delta", [(1, 1.0, 0.0), (2, 1.0, 0.0), (3, 1.0, 0.0),
                                             (1, 0.8, 0.0), (3, 1.2, 1.0)])
-def test_rayleigh_taylor_matches_linearised_scheme(mode, tau, delta):
+def test_rayleigh_taylor_matches_linearised_scheme(mode, tau, delta, forcing):
     """Hanging film (g < 0), gamma = 0.01, 128 x 2 (the mode is 1D): the
     fitted growth rate equals the dominant eigenvalue of the hand-linearised
-    step (unstable modes below k_c, damped above)."""
+    step (unstable modes below k_c, damped above), for Eq. (LBE) as printed
+    and for the second-order-forcing alternative."""
     h0, th, p = inputs.rayleigh_taylor(128, ny=2, mode=mode, g=-1e-4)
-    cfg = cfg_of(p, tau=tau, delta=delta)
+    cfg = cfg_of(p, tau=tau, delta=delta, forcing=forcing)
     k = 2 * math.pi * mode / 128
     sig = _mode_growth(cfg, O.kappa_field(cfg, th), h0, k, 12000, 1000, 2000)
-    ref = LT.scheme_growth_rate(k, 1.0, -1e-4, 0.01, tau, delta)
+    ref = LT.scheme_growth_rate(k, 1.0, -1e-4, 0.01, tau, delta, forcing=forcing)
     assert abs(sig - ref) <= 1e-4 * abs(ref)
+
+
+def test_rayleigh_taylor_config1_against_eq_rtgrowth():
+    """Config 1 (128^2 hanging film, g = -1e-4, gamma = 0.01, delta = 0,
+    tau = 1, seeded mode k = 2 pi/128, 2000 steps): Eq. (RTgrowth) gives
+    3.658e-7 per step.  The second-order-forcing reading reproduces it
+    within 1%; Eq. (LBE) as printed, with its explicit friction
+    (lambda = nu alpha / h = 1/2 per step at h0 = 1), grows at 0.67 of it,
+    as its own linearisation predicts.  Section III A
+    reports growth rates and critical wavenumbers that agree with Eq.
+    (RTgrowth), i.e. the behaviour of the second-order reading."""
+    h0, th, p = inputs.rayleigh_taylor(128, mode=1, g=-1e-4)
+    k = 2 * math.pi / 128
+    eq = LT.rt_growth_rate(k, 1.0, 1e-4, 0.01, 1.0 / 6.0)
+    fits = {}
+    for forcing in (0, 1):
+        cfg = cfg_of(p, ny=2, forcing=forcing)
+        fits[forcing] = _mode_growth(cfg, O.kappa_field(cfg, 0.0), h0[:2], k, 2000, 100, 100)
+    assert abs(fits[1] / eq - 1) <= 0.01
+    lin0 = LT.scheme_growth_rate(k, 1.0, -1e-4, 0.01, 1.0, 0.0, forcing=0)
+    assert abs(fits[0] / lin0 - 1) <= 1e-3
+    assert 0.6 < fits[0] / eq < 0.75
+
+
+def _neutral_wavenumber(cfg, nx, g, gamma):
+    """Neutral wavenumber of the hanging film from the oracle: growth rates
+    of the two lattice modes that bracket sqrt(|g|/gamma), interpolated
+    linearly in k^2 (near k_c the rate is ~ k^2 (k_c^2 - k^2))."""
+    kc0 = math.sqrt(g / gamma)
+    rates = []
+    for mode in range(int(kc0 * nx / (2 * math.pi) * 0.8), int(kc0 * nx / (2 * math.pi) * 1.05) + 2):
+        h0, th, p = inputs.rayleigh_taylor(nx, ny=2, mode=mode, g=-g, gamma=gamma)
+        k = 2 * math.pi * mode / nx
+        rates.append((k, _mode_growth(cfg, O.kappa_field(cfg, th), h0, k, 8000, 1000, 2000) / (k * k)))
+    for (k1, s1), (k2, s2) in zip(rates, rates[1:]):
+        if s1 > 0 >= s2:
+            return math.sqrt(k1 * k1 + s1 * (k2 * k2 - k1 * k1) / (s1 - s2))
+    raise AssertionError(f"no sign change in {rates}")
+
+
+def test_golden_rt_critical_wavenumber_no_slip():
+    """Section III A's printed k_c = 0.06 / 0.09 at |g| = 4e-5 / 8e-5,
+    gamma = 0.01, with config 1's no-slip substrate (delta = 0) and tau = 1:
+    the neutral wavenumber of the second-order reading rounds to the printed
+    values; that of Eq. (LBE) as printed is shifted by sqrt(1 - lambda/2) =
+    0.866 (lambda = 1/2) to 0.055 / 0.077."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "rt_critical_wavenumber.txt"))
+            if l.strip() and not l.startswith("#")]
+    for gamma, g, kc_printed in ((float(a), float(b), float(c)) for a, b, c in rows):
+        base = dict(nx=1024, ny=2, tau=1.0, gamma=gamma, g=-g, delta=0.0, n_exp=3, m_exp=2)
+        kc2 = _neutral_wavenumber(O.Config(**base, forcing=1), 1024, g, gamma)
+        kc1 = _neutral_wavenumber(O.Config(**base, forcing=0), 1024, g, gamma)
+        assert round(kc2, 2) == kc_printed, kc2
+        assert abs(kc1 / (math.sqrt(g / gamma) * math.sqrt(1 - 0.25)) - 1) <= 0.02, kc1
+        assert round(kc1, 2) != kc_printed
 
 
 def test_rayleigh_taylor_continuum_limit():
