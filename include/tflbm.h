@@ -82,8 +82,13 @@ enum {
 enum {
     TF_LBM_STATUS_NONFINITE = 1,  /* some population or h is NaN or inf */
     TF_LBM_STATUS_NONPOSITIVE = 2, /* some h <= 0 (Pi and alpha singular) */
-    TF_LBM_STATUS_TIMEOUT = 4      /* a step kernel gave up waiting for its
+    TF_LBM_STATUS_TIMEOUT = 4,     /* a step kernel gave up waiting for its
                                       own bulk copies (results invalid)    */
+    TF_LBM_STATUS_BOUNDS = 8       /* bounds-checked debug build only
+                                      (compiled with TFLBM_CHECK_BOUNDS): a
+                                      step kernel computed an index outside
+                                      its buffer; the access was redirected
+                                      to element 0 (results invalid)       */
 };
 
 /* Physical and numerical parameters (lattice units, dx = dt = 1). */

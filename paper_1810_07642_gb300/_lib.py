@@ -16,6 +16,7 @@ TF_LBM_OK = 0
 TF_LBM_ERR_ARG, TF_LBM_ERR_CUDA, TF_LBM_ERR_NOMEM = -1, -2, -3
 TF_LBM_ERR_NONFINITE, TF_LBM_ERR_UNSUPPORTED = -4, -5
 TF_LBM_STATUS_NONFINITE, TF_LBM_STATUS_NONPOSITIVE, TF_LBM_STATUS_TIMEOUT = 1, 2, 4
+TF_LBM_STATUS_BOUNDS = 8
 
 EXPORTED = [
     "tf_lbm_init", "tf_lbm_step", "tf_lbm_moments", "tf_lbm_pressure_force", "tf_lbm_mass",
@@ -67,15 +68,18 @@ _VP = ctypes.c_void_p
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the in-tree build, or the build named
+    by the TFLBM_LIBRARY environment variable (e.g. the bounds-checked debug
+    build, paper_1810_07642_gb300.build.LIB_CHECKED)."""
+    return os.environ.get("TFLBM_LIBRARY") or _build.LIB
 
 
 def lib():
-    """Load the in-tree libtflbm; raise if it has not been built."""
+    """Load the library (see library_path); raise if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"libtflbm is not built ({path} missing): run "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")

@@ -126,7 +126,7 @@ k_adjoint_march(const T* __restrict__ fin0, const SM* __restrict__ finm, const T
             const T* hs = hsm[(m - dir) & 7];
             const T kap = kappa ? kappa[(long long)am * nx + x] : C.kappa_u;
             const T ih = fdiv(T(1), hc[t] + C.href);
-            psm[m & 3][t] = film_pressure(hn, hc, hs, t, kap, ih, C, disj);
+            psm[m & 3][t] = film_pressure(hn, hc, hs, t, kap, ih, C, disj, BX);
         }
         // ---- C: force adjoint at row r(k-3)
         if (runC) {

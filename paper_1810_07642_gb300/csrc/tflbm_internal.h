@@ -27,6 +27,33 @@ constexpr int kStatusTimeout = 4;
 // Polls of one mbarrier before a bulk-copy kernel gives up (the default of
 // Consts::wait_limit).
 constexpr int kWaitLimit = 1 << 22;
+// Status bit of the bounds-checked debug build (TFLBM_CHECK_BOUNDS): a step
+// kernel computed an index outside the buffer it was meant for.
+constexpr int kStatusBounds = 8;
+
+// Index checks of the step kernels.  In a build with TFLBM_CHECK_BOUNDS
+// defined, TFLBM_IDX(i, n, st) compares i with [0, n): outside it sets
+// kStatusBounds in the status word st and yields 0 instead, so the access
+// stays inside the buffer and nothing traps; TFLBM_CHECK(cond, st) sets the
+// bit when cond is false.  In the normal build both compile to nothing.
+#if defined(TFLBM_CHECK_BOUNDS) && defined(__CUDACC__)
+__device__ __forceinline__ long long checked_index(long long i, long long n, int* status)
+{
+    if (i >= 0 && i < n) return i;
+    if (status) atomicOr(status, kStatusBounds);
+    return 0;
+}
+#define TFLBM_IDX(i, n, st) ((decltype(i))::tflbm::checked_index((long long)(i), (long long)(n), (st)))
+#define TFLBM_CHECK(cond, st)                                  \
+    do {                                                      \
+        if (!(cond) && (st)) atomicOr((st), ::tflbm::kStatusBounds); \
+    } while (0)
+#else
+#define TFLBM_IDX(i, n, st) (i)
+#define TFLBM_CHECK(cond, st) \
+    do {                      \
+    } while (0)
+#endif
 
 // Per-run constants of the step, in the compute type T.
 template <typename T>

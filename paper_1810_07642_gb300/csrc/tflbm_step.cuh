@@ -153,15 +153,19 @@ __device__ __forceinline__ void pull9(const T* __restrict__ f0, const SM* __rest
                                       int plane, int i0, int im, int ip, int dm, int dp,
                                       const Consts<T>& C, T (&v)[9])
 {
-    v[0] = ldro(f0 + i0);
-    v[1] = load_moving(ldro(fm + im), 1, C);
-    v[2] = load_moving(ldro(fm + (plane + im + dm)), 2, C);
-    v[3] = load_moving(ldro(fm + (2 * plane + i0 + dm)), 3, C);
-    v[4] = load_moving(ldro(fm + (3 * plane + ip + dm)), 4, C);
-    v[5] = load_moving(ldro(fm + (4 * plane + ip)), 5, C);
-    v[6] = load_moving(ldro(fm + (5 * plane + ip + dp)), 6, C);
-    v[7] = load_moving(ldro(fm + (6 * plane + i0 + dp)), 7, C);
-    v[8] = load_moving(ldro(fm + (7 * plane + im + dp)), 8, C);
+    const long long m8 = 8LL * plane;  // extent of the moving planes
+    int* st = C.status;
+    v[0] = ldro(f0 + TFLBM_IDX(i0, plane, st));
+    v[1] = load_moving(ldro(fm + TFLBM_IDX(im, m8, st)), 1, C);
+    v[2] = load_moving(ldro(fm + TFLBM_IDX(plane + im + dm, m8, st)), 2, C);
+    v[3] = load_moving(ldro(fm + TFLBM_IDX(2 * plane + i0 + dm, m8, st)), 3, C);
+    v[4] = load_moving(ldro(fm + TFLBM_IDX(3 * plane + ip + dm, m8, st)), 4, C);
+    v[5] = load_moving(ldro(fm + TFLBM_IDX(4 * plane + ip, m8, st)), 5, C);
+    v[6] = load_moving(ldro(fm + TFLBM_IDX(5 * plane + ip + dp, m8, st)), 6, C);
+    v[7] = load_moving(ldro(fm + TFLBM_IDX(6 * plane + i0 + dp, m8, st)), 7, C);
+    v[8] = load_moving(ldro(fm + TFLBM_IDX(7 * plane + im + dp, m8, st)), 8, C);
+    (void)m8;
+    (void)st;
 }
 
 // dh = sum_l v_l with v_0 = f_0 - href: the moving populations are summed
@@ -182,8 +186,10 @@ __device__ __forceinline__ T sum9(const T (&v)[9], T& err)
 // ih = 1/h of the node.
 template <typename T>
 __device__ __forceinline__ T film_pressure(const T* hn, const T* hc, const T* hs_, int j, T kap,
-                                           T ih, const Consts<T>& C, bool disj)
+                                           T ih, const Consts<T>& C, bool disj, int n)
 {
+    TFLBM_CHECK(j >= 1 && j + 1 < n, C.status);  // the ring rows hold n columns
+    (void)n;
     const T axis = (hc[j - 1] + hc[j + 1]) + (hn[j] + hs_[j]);
     const T diag = (hn[j - 1] + hn[j + 1]) + (hs_[j - 1] + hs_[j + 1]);
     T lap = (T(4) * axis + diag - T(20) * hc[j]) * T(1.0 / 6.0);
@@ -201,9 +207,11 @@ template <typename SM, typename T, bool OMEGA1>
 __device__ __forceinline__ void collide_store(const T* pn, const T* pc, const T* ps, int t, T dh,
                                               T ih, T jx, T jy, T er, const T (&f)[9],
                                               T* __restrict__ fout0, SM* __restrict__ foutm,
-                                              int row, int x, int plane, const Consts<T>& C)
+                                              int row, int x, int plane, const Consts<T>& C, int n)
 {
     constexpr bool NARROW = !std::is_same<SM, T>::value;
+    TFLBM_CHECK(t >= 1 && t + 1 < n, C.status);  // the p ring rows hold n columns
+    (void)n;
     const T third = T(1.0 / 3.0), twelfth = T(1.0 / 12.0), sixth = T(1.0 / 6.0);
     // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
     const T gpx = (pc[t + 1] - pc[t - 1]) * third
@@ -304,16 +312,19 @@ __device__ __forceinline__ void collide_store(const T* pn, const T* pc, const T*
         q1 = o1; q2 = o2; q3 = o3; q4 = o4; q5 = o5; q6 = o6; q7 = o7; q8 = o8;
     }
     const int i = row + x;
-    fout0[i] = o0v;
-    SM* om = foutm + i;
-    om[0] = q1;
-    om[plane] = q2;
-    om[2 * plane] = q3;
-    om[3 * plane] = q4;
-    om[4 * plane] = q5;
-    om[5 * plane] = q6;
-    om[6 * plane] = q7;
-    om[7 * plane] = q8;
+    const long long m8 = 8LL * plane;
+    int* st = C.status;
+    fout0[TFLBM_IDX(i, plane, st)] = o0v;
+    foutm[TFLBM_IDX(i, m8, st)] = q1;
+    foutm[TFLBM_IDX(plane + i, m8, st)] = q2;
+    foutm[TFLBM_IDX(2 * plane + i, m8, st)] = q3;
+    foutm[TFLBM_IDX(3 * plane + i, m8, st)] = q4;
+    foutm[TFLBM_IDX(4 * plane + i, m8, st)] = q5;
+    foutm[TFLBM_IDX(5 * plane + i, m8, st)] = q6;
+    foutm[TFLBM_IDX(6 * plane + i, m8, st)] = q7;
+    foutm[TFLBM_IDX(7 * plane + i, m8, st)] = q8;
+    (void)m8;
+    (void)st;
 }
 
 // ---------------------------------------------------------------------------
@@ -422,15 +433,19 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
             const int i0 = r0 + x, im = r0 + xm, ip = r0 + xp;
             T(&d)[9][ASYNC ? BX : 1] = stg[st];
             constexpr int E = sizeof(T);
-            cp_async<E>(&d[0][t], fin0 + i0);
-            cp_async<E>(&d[1][t], finm + im);
-            cp_async<E>(&d[2][t], finm + (plane + im + dm));
-            cp_async<E>(&d[3][t], finm + (2 * plane + i0 + dm));
-            cp_async<E>(&d[4][t], finm + (3 * plane + ip + dm));
-            cp_async<E>(&d[5][t], finm + (4 * plane + ip));
-            cp_async<E>(&d[6][t], finm + (5 * plane + ip + dp));
-            cp_async<E>(&d[7][t], finm + (6 * plane + i0 + dp));
-            cp_async<E>(&d[8][t], finm + (7 * plane + im + dp));
+            const long long m8 = 8LL * plane;
+            int* cs = C.status;
+            cp_async<E>(&d[0][t], fin0 + TFLBM_IDX(i0, plane, cs));
+            cp_async<E>(&d[1][t], finm + TFLBM_IDX(im, m8, cs));
+            cp_async<E>(&d[2][t], finm + TFLBM_IDX(plane + im + dm, m8, cs));
+            cp_async<E>(&d[3][t], finm + TFLBM_IDX(2 * plane + i0 + dm, m8, cs));
+            cp_async<E>(&d[4][t], finm + TFLBM_IDX(3 * plane + ip + dm, m8, cs));
+            cp_async<E>(&d[5][t], finm + TFLBM_IDX(4 * plane + ip, m8, cs));
+            cp_async<E>(&d[6][t], finm + TFLBM_IDX(5 * plane + ip + dp, m8, cs));
+            cp_async<E>(&d[7][t], finm + TFLBM_IDX(6 * plane + i0 + dp, m8, cs));
+            cp_async<E>(&d[8][t], finm + TFLBM_IDX(7 * plane + im + dp, m8, cs));
+            (void)m8;
+            (void)cs;
         }
         cp_async_commit();
     };
@@ -440,7 +455,9 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
     } else {
         if (B.hcol) pull_row(wm1, w0, w1);
     }
-    if (KFIELD && B.pcol) kap_n = kappa[(long long)wm1 * nx + x];
+    const long long nkap = (long long)nx * ny;  // kappa field extent
+    (void)nkap;
+    if (KFIELD && B.pcol) kap_n = kappa[TFLBM_IDX((long long)wm1 * nx + x, nkap, C.status)];
 
     auto body = [&](auto stage_c, int k) {
         constexpr int s = decltype(stage_c)::value;  // slot of row r(k) (and r(k-4))
@@ -475,14 +492,14 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
                 for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
             }
             if (!ASYNC && k + 1 <= R + 3) pull_row(w0, w1, w2);
-            if (KFIELD && B.pcol) kap_n = kappa[(long long)w0 * nx + x];
+            if (KFIELD && B.pcol) kap_n = kappa[TFLBM_IDX((long long)w0 * nx + x, nkap, C.status)];
         }
         __syncthreads();
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
         if (B.pcol && k >= 2 && k <= R + 3) {
             const T ih = fdiv(T(1), hsm[s1][t] + C.href);
             ihv[s1] = ih;
-            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj);
+            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj, BX);
         }
         // ---- (B2) force, collision and store of row r(k-3) (needs p rows r(k-4) .. r(k-2))
         if (B.ocol && k >= 5) {
@@ -500,7 +517,7 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
             }
             collide_store<SM, T, OMEGA1>(dir > 0 ? psm[s2] : psm[s], psm[s3], dir > 0 ? psm[s] : psm[s2], t,
                                          hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fl,
-                                         fout0, foutm, o * pitch, x, plane, C);
+                                         fout0, foutm, o * pitch, x, plane, C, BX);
         }
         wm1 = w0;
         w0 = w1;
@@ -662,9 +679,12 @@ __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b :
 template <typename SM, typename T>
 __device__ __noinline__ void issue_step(unsigned char* stage, uint64_t* bar, const T* fin0,
                                         const SM* finm, int plane, int pitch, int nx, int ny, int row,
-                                        int a0, int a1, int b0, int bm, uint32_t bytes)
+                                        int a0, int a1, int b0, int bm, uint32_t bytes, int* status)
 {
     const int lane = threadIdx.x & 31;
+    // the periodic images taken left and right of the row must lie in it
+    TFLBM_CHECK(a0 >= -nx && a1 <= 2 * nx && a0 < a1, status);
+    (void)status;
     if (lane == 0) mbar_arrive_tx(bar, bytes);
     __syncwarp();
     if (lane < 9) {
@@ -724,7 +744,7 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
     auto issue = [&](int j) {  // march step j (h row r(j)) into stage j % kStages
         const int st = j & (kStages - 1);
         issue_step<SM, T>(stage_mem + st * L::STAGE, &bars[st], fin0, finm, plane, pitch, nx, ny,
-                          wrap_index(B.rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step);
+                          wrap_index(B.rstart + j * dir, ny), a0, a1, L::B0, L::BM, bytes_step, C.status);
     };
     bool gave_up = false;  // this thread stopped waiting for a stage
 
@@ -739,7 +759,9 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
 
     int wk = wrap_index(B.rstart, ny);  // wrapped index of row r(k)
     T kap_n = C.kappa_u;
-    if (KFIELD && B.pcol) kap_n = kappa[(long long)wrap_index(B.rstart - dir, ny) * nx + x];
+    const long long nkap = (long long)nx * ny;  // kappa field extent
+    (void)nkap;
+    if (KFIELD && B.pcol) kap_n = kappa[TFLBM_IDX((long long)wrap_index(B.rstart - dir, ny) * nx + x, nkap, C.status)];
     T fv[4][9];
     T jxv[4], jyv[4], ihv[4], erv[4];
 #pragma unroll
@@ -773,15 +795,18 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
                 constexpr int M = L::LMAX;
                 // population l at column X comes from X - c_lx
                 T v[9];
-                v[0] = p0[col];
-                v[1] = load_moving(pm[0 * M + col - 1], 1, C);
-                v[2] = load_moving(pm[1 * M + col - 1], 2, C);
-                v[3] = load_moving(pm[2 * M + col], 3, C);
-                v[4] = load_moving(pm[3 * M + col + 1], 4, C);
-                v[5] = load_moving(pm[4 * M + col + 1], 5, C);
-                v[6] = load_moving(pm[5 * M + col + 1], 6, C);
-                v[7] = load_moving(pm[6 * M + col], 7, C);
-                v[8] = load_moving(pm[7 * M + col - 1], 8, C);
+                // the stage holds M columns per plane; col - 1 .. col + 1 are read
+                TFLBM_CHECK(col >= 1 && col + 1 < M, C.status);
+                const int cc = TFLBM_IDX(col, M, C.status);
+                v[0] = p0[cc];
+                v[1] = load_moving(pm[0 * M + cc - 1], 1, C);
+                v[2] = load_moving(pm[1 * M + cc - 1], 2, C);
+                v[3] = load_moving(pm[2 * M + cc], 3, C);
+                v[4] = load_moving(pm[3 * M + cc + 1], 4, C);
+                v[5] = load_moving(pm[4 * M + cc + 1], 5, C);
+                v[6] = load_moving(pm[5 * M + cc + 1], 6, C);
+                v[7] = load_moving(pm[6 * M + cc], 7, C);
+                v[8] = load_moving(pm[7 * M + cc - 1], 8, C);
                 hsm[s][t] = sum9(v, erv[s]);
                 jxv[s] = ((v[1] + v[2]) + v[8]) - ((v[4] + v[5]) + v[6]);
                 jyv[s] = ((v[2] + v[3]) + v[4]) - ((v[6] + v[7]) + v[8]);
@@ -789,7 +814,8 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
 #pragma unroll
                     for (int l = 0; l < 9; ++l) fv[s][l] = v[l];
                 }
-                if (KFIELD && B.pcol) kap_n = kappa[(long long)wk * nx + x];  // row r(k), used next step
+                if (KFIELD && B.pcol)  // row r(k), used next step
+                    kap_n = kappa[TFLBM_IDX((long long)wk * nx + x, nkap, C.status)];
             }
         }
         // every thread is done with this stage (or the CTA gives up): refill
@@ -800,14 +826,14 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
         if (B.pcol && k >= 2 && k <= R + 3) {
             const T ih = fdiv(T(1), hsm[s1][t] + C.href);
             ihv[s1] = ih;
-            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj);
+            psm[s1][t] = film_pressure(hsm[s], hsm[s1], hsm[s2], t, kap, ih, C, disj, BX);
         }
         // ---- (B2) force, collision and store of row r(k-3)
         if (B.ocol && k >= 5) {
             const int o = B.rstart + (k - 3) * dir;
             collide_store<SM, T, OMEGA1>(dir > 0 ? psm[s2] : psm[s], psm[s3], dir > 0 ? psm[s] : psm[s2], t,
                                          hsm[s3][t], ihv[s3], jxv[s3], jyv[s3], erv[s3], fv[s3],
-                                         fout0, foutm, o * pitch, x, plane, C);
+                                         fout0, foutm, o * pitch, x, plane, C, BX);
         }
         wk += dir;
         wk = wk == ny ? 0 : (wk < 0 ? ny - 1 : wk);

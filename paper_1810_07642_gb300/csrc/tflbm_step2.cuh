@@ -204,8 +204,11 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
     }
     // stored rest population f*_0 - href = (h - href) - sum_{l>0} f*_l, with
     // the exact residuals folded back as in collide_store
-    V* om = reinterpret_cast<V*>(foutm) + (i >> 1);
-    const int hp = plane >> 1;
+    const int hp = plane >> 1;  // pairs per plane
+    // the pair (i, i+1) of plane 0 and of the eight moving planes
+    TFLBM_CHECK(i >= 0 && (i & 1) == 0 && i + 1 < plane, C.status);
+    const int ip = TFLBM_IDX(i >> 1, hp, C.status);
+    V* om = reinterpret_cast<V*>(foutm) + ip;
     if constexpr (!NARROW) {
         const float2 osum = padd(padd(padd(o1, o5), padd(o3, o7)), padd(padd(o2, o6), padd(o4, o8)));
         float2 o0v, e2;
@@ -213,7 +216,7 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
         const float2 half_r = pmul(padd(er, e2), pk(0.5f));
         o1 = padd(o1, half_r);
         o5 = padd(o5, half_r);
-        reinterpret_cast<float2*>(fout0)[i >> 1] = o0v;
+        reinterpret_cast<float2*>(fout0)[ip] = o0v;
         om[0] = o1; om[hp] = o2; om[2 * hp] = o3; om[3 * hp] = o4;
         om[4 * hp] = o5; om[5 * hp] = o6; om[6 * hp] = o7; om[7 * hp] = o8;
     } else {
@@ -242,7 +245,7 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
         const V q1l = narrow_pair<SM>(o1l, Rax, NRa, C);
         const uint32_t mask = (lx ? 0x0000ffffu : 0u) | (ly ? 0xffff0000u : 0u);
         const V q1 = from_bits<V>((bits(q1l) & mask) | (bits(q1r) & ~mask));
-        reinterpret_cast<float2*>(fout0)[i >> 1] = o0n;
+        reinterpret_cast<float2*>(fout0)[ip] = o0n;
         om[0] = q1; om[hp] = q2; om[2 * hp] = q3; om[3 * hp] = q4;
         om[4 * hp] = q5; om[5 * hp] = q6; om[6 * hp] = q7; om[7 * hp] = q8;
     }
@@ -320,26 +323,33 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         constexpr int b = decltype(b_c)::value;
         const int ys = dir > 0 ? wb : wa, yn = dir > 0 ? wa : wb;  // rows y-1, y+1
         const int i0 = (w * pitch + c) >> 1, is = (ys * pitch + c) >> 1, in = (yn * pitch + c) >> 1;
-        q0[b] = ldpair(f0p + i0);
-        qm[b][0] = ldpair(fmp + i0);               // l = 1 from row y
-        qm[b][1] = ldpair(fmp + (half + is));      // l = 2 from row y-1
-        qm[b][2] = ldpair(fmp + (2 * half + is));  // l = 3
-        qm[b][3] = ldpair(fmp + (3 * half + is));  // l = 4
-        qm[b][4] = ldpair(fmp + (4 * half + i0));  // l = 5 from row y
-        qm[b][5] = ldpair(fmp + (5 * half + in));  // l = 6 from row y+1
-        qm[b][6] = ldpair(fmp + (6 * half + in));  // l = 7
-        qm[b][7] = ldpair(fmp + (7 * half + in));  // l = 8
+        const long long m8 = 8LL * half;  // pairs of the eight moving planes
+        int* st = C.status;
+        q0[b] = ldpair(f0p + TFLBM_IDX(i0, half, st));
+        qm[b][0] = ldpair(fmp + TFLBM_IDX(i0, m8, st));               // l = 1 from row y
+        qm[b][1] = ldpair(fmp + TFLBM_IDX(half + is, m8, st));        // l = 2 from row y-1
+        qm[b][2] = ldpair(fmp + TFLBM_IDX(2 * half + is, m8, st));    // l = 3
+        qm[b][3] = ldpair(fmp + TFLBM_IDX(3 * half + is, m8, st));    // l = 4
+        qm[b][4] = ldpair(fmp + TFLBM_IDX(4 * half + i0, m8, st));    // l = 5 from row y
+        qm[b][5] = ldpair(fmp + TFLBM_IDX(5 * half + in, m8, st));    // l = 6 from row y+1
+        qm[b][6] = ldpair(fmp + TFLBM_IDX(6 * half + in, m8, st));    // l = 7
+        qm[b][7] = ldpair(fmp + TFLBM_IDX(7 * half + in, m8, st));    // l = 8
         if (edge) {
-            qe[b][0] = ldpair(fmp + ((e0 + w * pitch + ce) >> 1));
-            qe[b][1] = ldpair(fmp + ((e1 + ys * pitch + ce) >> 1));
-            qe[b][2] = ldpair(fmp + ((e2 + yn * pitch + ce) >> 1));
+            qe[b][0] = ldpair(fmp + TFLBM_IDX((e0 + w * pitch + ce) >> 1, m8, st));
+            qe[b][1] = ldpair(fmp + TFLBM_IDX((e1 + ys * pitch + ce) >> 1, m8, st));
+            qe[b][2] = ldpair(fmp + TFLBM_IDX((e2 + yn * pitch + ce) >> 1, m8, st));
         }
+        (void)m8;
+        (void)st;
     };
 
     float2 kap_n = pk(C.kappa_u);
     load_row(std::integral_constant<int, 0>{}, wm1, w0, w1);
     if constexpr (PF == 2) load_row(std::integral_constant<int, 1>{}, w0, w1, w2);
-    if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)wm1 * nx + c));
+    const long long npair = (long long)nx * ny / 2;  // kappa field extent in pairs (nx even)
+    (void)npair;
+    if (KFIELD && pcol)
+        kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)wm1 * nx + c) >> 1, npair, C.status)];
 
     // ring slots no thread writes (outer halves of the edge columns' stencils)
     if (t < 4) {
@@ -378,7 +388,9 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 } else {
                     if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
                 }
-                if (KFIELD && pcol) kap_n = *reinterpret_cast<const float2*>(kappa + ((long long)w0 * nx + c));
+                if (KFIELD && pcol)
+                    kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)w0 * nx + c) >> 1, npair,
+                                                                              C.status)];
                 // l = 1, 2, 8 arrive from the left, l = 4, 5, 6 from the right
                 float u1 = __shfl_up_sync(0xffffffffu, v[0].y, 1);
                 float u2 = __shfl_up_sync(0xffffffffu, v[1].y, 1);
@@ -411,6 +423,8 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         __syncthreads();
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
         if (pcol && k >= 2 && k <= R + 3) {
+            // the stencil reads slots OFF + 2t - 1 .. OFF + 2t + 2 of rings of NC + 4
+            TFLBM_CHECK(OFF + 2 * t - 1 >= 0 && OFF + 2 * t + 2 < NC + 4, C.status);
             float2 ih;
             const float2 p = pair_pressure(hsm[s] + OFF + 2 * t, hsm[s1] + OFF + 2 * t, hsm[s2] + OFF + 2 * t, kap,
                                            disj, C, ih);
@@ -420,6 +434,7 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         // ---- (B2) force, collision and store of row r(k-3)
         if (ocol && k >= 5) {
             const int o = rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
+            TFLBM_CHECK(OFF + 2 * t - 1 >= 0 && OFF + 2 * t + 2 < NC + 4 && o >= 0 && o < ny, C.status);
             const float* pn = (dir > 0 ? psm[s2] : psm[s]) + OFF + 2 * t;  // row o+1
             const float* pc = psm[s3] + OFF + 2 * t;
             const float* ps = (dir > 0 ? psm[s] : psm[s2]) + OFF + 2 * t;  // row o-1

@@ -247,6 +247,30 @@ def test_full_size_patterned_2048_sampled_against_oracle():
     assert worst <= 1e-5, worst
 
 
+def test_full_size_patterned_2048_1000_steps_every_storage_type():
+    """Config 3's own lattice (2048 x 2048 chemically patterned dewetting,
+    Sec. III D shape) for 1000 steps in FP32, FP16 and BF16 storage in the
+    default launch shapes, against the whole FP64 oracle run (about a
+    minute on the host cores): relative Linf on h within the storage type's
+    tolerance and relative mass drift within 1e-6."""
+    h0, th, p = inputs.patterned_dewetting(2048, seed=0)
+    cfg = cfg_of(p)
+    f = O.init(cfg, h0)
+    O.step(cfg, O.kappa_field(cfg, th), f, 1000)
+    ho = f.sum(0)
+    for dtype in ("f32", "f16", "bf16"):
+        sim = ThinFilm(p, h0, th, dtype=dtype)
+        m0 = sim.mass()
+        sim.step(1000)
+        h = sim.h().double().cpu().numpy()
+        drift = abs(sim.mass() - m0) / m0
+        assert sim.check() == 0
+        sim.close()
+        err = rel_linf(h, ho)
+        assert err <= TOL[dtype], (dtype, err)
+        assert drift <= 1e-6, (dtype, drift)
+
+
 def test_full_size_mass_conservation_and_check():
     h0, th, p = inputs.patterned_dewetting(2048, seed=2)
     sim = ThinFilm(p, h0, th)
