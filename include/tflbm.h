@@ -97,6 +97,16 @@ typedef struct tf_lbm_params {
     int32_t dtype;        /* TF_LBM_F32, TF_LBM_F64, TF_LBM_F16 or TF_LBM_BF16   */
     int32_t n_exp, m_exp; /* exponents of Eq. (disjoiningP), n != m, >= 1     */
     int32_t pi_sign;      /* +1 physical (default) or -1 printed sign of Pi     */
+    int32_t forcing;      /* 0: Eq. (LBE) as printed (default): u = j/h, source
+                             3 w_l c_l.F.  1: second-order forcing (labelled
+                             alternative, not the printed equation): u =
+                             (j + F/2)/h with the friction taken at that
+                             velocity, u (h + nu alpha/2) = j + F'/2, and the
+                             source (1 - omega/2) w_l [3 (c_l - u) +
+                             9 (c_l.u) c_l].F.  It reproduces the growth
+                             rates and critical wavenumbers of Sec. III A
+                             (Eq. RTgrowth); forward steps only (the adjoint
+                             entry points reject it)                          */
     double tau;           /* relaxation time, > 1/2; omega = 1/tau             */
     double gamma;         /* surface tension                                    */
     double g;             /* gravity in the equilibria (g < 0: hanging film)    */

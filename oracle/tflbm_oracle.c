@@ -245,8 +245,33 @@ static void pressure_force(const orc_params* P, const double* kappa,
     }
 }
 
+/* The labelled second-order-forcing alternative (forcing = 1): the velocity
+ * u = (j + F/2)/h with the friction -nu alpha u taken at that velocity,
+ * u (h + nu alpha/2) = j + F'/2 (F' the film-pressure and body forces), and
+ * the total force F = F' - nu alpha u; overwrites ux, uy, Fx, Fy. */
+static void second_order_velocity_force(const orc_params* P, const double* f, const double* h,
+                                        const double* gpx, const double* gpy, double* ux, double* uy,
+                                        double* Fx, double* Fy)
+{
+    const int64_t N = (int64_t)P->nx * P->ny;
+    const double nu = (P->tau - 0.5) / 3.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double jx = 0.0, jy = 0.0;
+        for (int l = 0; l < 9; ++l) { jx += CX[l] * f[l * N + i]; jy += CY[l] * f[l * N + i]; }
+        const double a = orc_alpha(h[i], P->delta);
+        const double fpx = -h[i] * gpx[i] + h[i] * P->gx_body;
+        const double fpy = -h[i] * gpy[i] + h[i] * P->gy_body;
+        ux[i] = (jx + 0.5 * fpx) / (h[i] + 0.5 * nu * a);
+        uy[i] = (jy + 0.5 * fpy) / (h[i] + 0.5 * nu * a);
+        Fx[i] = fpx - nu * a * ux[i];
+        Fy[i] = fpy - nu * a * uy[i];
+    }
+}
+
 /* Film pressure and total force of the post-streaming state f, for
- * diagnostics.  Any output pointer may be NULL. */
+ * diagnostics (the force of the reading selected by P->forcing).  Any output
+ * pointer may be NULL. */
 void orc_pressure_force(const orc_params* P, const double* kappa, const double* f,
                         double* p_out, double* Fx_out, double* Fy_out)
 {
@@ -257,6 +282,7 @@ void orc_pressure_force(const orc_params* P, const double* kappa, const double* 
            *Fx = buf + 7 * N, *Fy = buf + 8 * N;
     orc_moments(P, f, h, ux, uy);
     pressure_force(P, kappa, h, ux, uy, lap, p, gpx, gpy, Fx, Fy);
+    if (P->forcing == 1) second_order_velocity_force(P, f, h, gpx, gpy, ux, uy, Fx, Fy);
     if (p_out) memcpy(p_out, p, sizeof(double) * N);
     if (Fx_out) memcpy(Fx_out, Fx, sizeof(double) * N);
     if (Fy_out) memcpy(Fy_out, Fy, sizeof(double) * N);
@@ -291,23 +317,7 @@ void orc_step(const orc_params* P, const double* kappa, double* f, int64_t nstep
         /* moments, pressure and force, all from time-t fields */
         orc_moments(P, f, h, ux, uy);
         pressure_force(P, kappa, h, ux, uy, lap, p, gpx, gpy, Fx, Fy);
-        if (P->forcing == 1) {
-            /* second-order forcing: u = (j + F/2)/h with the friction taken at
-             * that velocity, u (h + nu alpha/2) = j + F'/2 */
-            const double nu = (P->tau - 0.5) / 3.0;
-#pragma omp parallel for schedule(static)
-            for (int64_t i = 0; i < N; ++i) {
-                double jx = 0.0, jy = 0.0;
-                for (int l = 0; l < 9; ++l) { jx += CX[l] * f[l * N + i]; jy += CY[l] * f[l * N + i]; }
-                const double a = orc_alpha(h[i], P->delta);
-                const double fpx = -h[i] * gpx[i] + h[i] * P->gx_body;
-                const double fpy = -h[i] * gpy[i] + h[i] * P->gy_body;
-                ux[i] = (jx + 0.5 * fpx) / (h[i] + 0.5 * nu * a);
-                uy[i] = (jy + 0.5 * fpy) / (h[i] + 0.5 * nu * a);
-                Fx[i] = fpx - nu * a * ux[i];
-                Fy[i] = fpy - nu * a * uy[i];
-            }
-        }
+        if (P->forcing == 1) second_order_velocity_force(P, f, h, gpx, gpy, ux, uy, Fx, Fy);
         /* collision: (1 - omega) f + omega f_eq + source */
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {

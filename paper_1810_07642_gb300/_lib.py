@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dtype", ctypes.c_int32),
         ("n_exp", ctypes.c_int32), ("m_exp", ctypes.c_int32), ("pi_sign", ctypes.c_int32),
-        ("tau", ctypes.c_double), ("gamma", ctypes.c_double), ("g", ctypes.c_double),
+        ("forcing", ctypes.c_int32), ("tau", ctypes.c_double), ("gamma", ctypes.c_double), ("g", ctypes.c_double),
         ("delta", ctypes.c_double), ("hstar", ctypes.c_double), ("gx_body", ctypes.c_double),
         ("gy_body", ctypes.c_double), ("theta_uniform", ctypes.c_double),
     ]

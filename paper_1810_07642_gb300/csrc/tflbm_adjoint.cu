@@ -408,6 +408,8 @@ int tf_lbm_adjoint_step(tf_lbm_handle* H, const void* f_t, const void* a_next, v
     if (!f_t || !a_next || !a_t || !grad_kappa)
         return handle_fail(H, TF_LBM_ERR_ARG, "f_t, a_next, a_t and grad_kappa must not be NULL");
     if (a_t == a_next) return handle_fail(H, TF_LBM_ERR_ARG, "a_t must not alias a_next");
+    if (H->p.forcing != 0)
+        return handle_fail(H, TF_LBM_ERR_UNSUPPORTED, "the adjoint differentiates Eq. (LBE) as printed (forcing = 0)");
     cudaError_t e = adjoint_step_dispatch(H, f_t, a_next, a_t, grad_kappa, (cudaStream_t)stream);
     if (e != cudaSuccess) return handle_cuda_fail(H, e, "adjoint kernels");
     return TF_LBM_OK;
@@ -421,6 +423,8 @@ int tf_lbm_tape_create(tf_lbm_handle* H, const void* h0, const void* theta, int6
     *out = nullptr;
     if (!h0) return handle_fail(H, TF_LBM_ERR_ARG, "h0 must not be NULL");
     if (nsteps < 1) return handle_fail(H, TF_LBM_ERR_ARG, "nsteps must be >= 1");
+    if (H->p.forcing != 0)
+        return handle_fail(H, TF_LBM_ERR_UNSUPPORTED, "the adjoint differentiates Eq. (LBE) as printed (forcing = 0)");
     if (every <= 0) every = (int32_t)ceil(sqrt((double)nsteps));
     if (every > nsteps) every = (int32_t)nsteps;
     tf_lbm_tape* tp = new tf_lbm_tape();

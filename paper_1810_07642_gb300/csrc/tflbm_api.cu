@@ -89,6 +89,7 @@ int validate(const tf_lbm_params* p)
     if (p->n_exp < 1 || p->m_exp < 1 || p->n_exp > 64 || p->m_exp > 64) return bad("n_exp and m_exp must be in [1, 64]");
     if (p->n_exp == p->m_exp) return bad("n_exp must differ from m_exp");
     if (p->pi_sign != 1 && p->pi_sign != -1) return bad("pi_sign must be +1 or -1");
+    if (p->forcing != 0 && p->forcing != 1) return bad("forcing must be 0 or 1");
     if (!isfinite(p->gamma) || !isfinite(p->g) || !isfinite(p->gx_body) || !isfinite(p->gy_body) ||
         !isfinite(p->theta_uniform) || !isfinite(p->tau))
         return bad("non-finite parameter");
@@ -185,6 +186,7 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.m_exp = H->p.m_exp;
     C.status = H->status;
     C.wait_limit = H->wait_limit;
+    C.forcing = H->p.forcing;
     return C;
 }
 

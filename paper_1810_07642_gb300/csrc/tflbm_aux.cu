@@ -199,8 +199,18 @@ __global__ void k_pf_f(Pops<T, SM> P, const T* __restrict__ pbuf, T* p, T* fx, T
     const T fr = C.nu6 / (T(2) * hh * hh + T(6) * C.delta * hh + T(3) * C.delta * C.delta);
     const long long i = (long long)y * G.nx + x;
     if (p) p[i] = Pp(y, x);
-    if (fx) fx[i] = -hh * gpx - fr * jx + hh * C.gx;
-    if (fy) fy[i] = -hh * gpy - fr * jy + hh * C.gy;
+    T Fx = -hh * gpx - fr * jx + hh * C.gx;
+    T Fy = -hh * gpy - fr * jy + hh * C.gy;
+    if (C.forcing) {
+        // second-order forcing: friction at u = (j + F/2)/h, i.e.
+        // h u (1 + fr/2) = j + F'/2 with F' the force without friction
+        const T fpx = hh * (C.gx - gpx), fpy = hh * (C.gy - gpy);
+        const T q = T(1) / (T(1) + T(0.5) * fr);
+        Fx = fpx - fr * (jx + T(0.5) * fpx) * q;
+        Fy = fpy - fr * (jy + T(0.5) * fpy) * q;
+    }
+    if (fx) fx[i] = Fx;
+    if (fy) fy[i] = Fy;
 }
 
 // Neumaier pair (s, c): value s + c.

@@ -75,6 +75,7 @@ struct Consts {
     int n_exp, m_exp;
     int* status;     // device word for kStatusTimeout (may be null)
     int wait_limit;  // polls of one mbarrier before giving up (<= 0: give up at once)
+    int forcing;     // 0: Eq. (LBE) as printed; 1: second-order forcing
 };
 
 // Launch shape of the fused step.

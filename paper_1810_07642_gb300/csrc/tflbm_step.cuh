@@ -222,40 +222,79 @@ __device__ __forceinline__ void collide_store(const T* pn, const T* pc, const T*
     // Eqs. (force), (forcefric), (alphafric):
     // nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
     const T fr = fdiv(C.nu6, h * (T(2) * h + T(6) * C.delta) + T(3) * C.delta * C.delta);
-    const T Fx = h * (C.gx - gpx) - fr * jx;
-    const T Fy = h * (C.gy - gpy) - fr * jy;
+    // Eq. (LBE) as printed: u = j/h and F with the friction at that velocity.
+    // Second-order forcing (C.forcing): u = (j + F/2)/h with the friction
+    // taken at that velocity, u (h + nu alpha/2) = j + F'/2; the equilibria
+    // then use h u in place of j.
+    T Fx, Fy, ux, uy, ex, ey;
+    if (C.forcing) {
+        const T fpx = h * (C.gx - gpx), fpy = h * (C.gy - gpy);
+        const T q = fdiv(ih, T(1) + T(0.5) * fr);  // 1 / (h + nu alpha / 2)
+        ux = (jx + T(0.5) * fpx) * q;
+        uy = (jy + T(0.5) * fpy) * q;
+        ex = h * ux;
+        ey = h * uy;
+        Fx = fpx - fr * ex;
+        Fy = fpy - fr * ey;
+    } else {
+        Fx = h * (C.gx - gpx) - fr * jx;
+        Fy = h * (C.gy - gpy) - fr * jy;
+        ux = jx * ih;
+        uy = jy * ih;
+        ex = jx;
+        ey = jy;
+    }
     // Eq. (equilibria) with e^2 = 1, written as S +- D per pair of opposite
     // directions; source 3 w_l c_l . F.
-    const T ux = jx * ih, uy = jy * ih;
     const T A = h * (C.g * h - (ux * ux + uy * uy)) * sixth;
-    const T Sx = A + T(0.5) * jx * ux;
-    const T Sy = A + T(0.5) * jy * uy;
+    T Sx = A + T(0.5) * ex * ux;
+    T Sy = A + T(0.5) * ey * uy;
     const T a = ux + uy, b = uy - ux;
-    const T Sa = (A + T(0.5) * h * a * a) * T(0.25);
-    const T Sb = (A + T(0.5) * h * b * b) * T(0.25);
+    T Sa = (A + T(0.5) * h * a * a) * T(0.25);
+    T Sb = (A + T(0.5) * h * b * b) * T(0.25);
+    // second-order source (1 - omega/2) w_l [3 (c_l - u) + 9 (c_l.u) c_l].F:
+    // its odd part is the printed 3 w_l c_l.F scaled by (1 - omega/2), its
+    // even part T per pair of opposite directions
+    T Tx = T(0), Ty = T(0), Ta = T(0), Tb = T(0);
+    if (C.forcing) {
+        const T ks = T(1) - T(0.5) * C.omega;
+        Fx *= ks;
+        Fy *= ks;
+        const T uF3 = (ux * Fx + uy * Fy) * third;
+        Tx = ux * Fx - uF3;
+        Ty = uy * Fy - uF3;
+        Ta = (a * (Fx + Fy) - uF3) * T(0.25);
+        Tb = (b * (Fy - Fx) - uF3) * T(0.25);
+        if (OMEGA1) {
+            Sx += Tx;
+            Sy += Ty;
+            Sa += Ta;
+            Sb += Tb;
+        }
+    }
     T o1, o2, o3, o4, o5, o6, o7, o8;
     if (OMEGA1) {
-        const T Dx = (jx + Fx) * third, Dy = (jy + Fy) * third;
-        const T Da = ((jx + jy) + (Fx + Fy)) * twelfth;
-        const T Db = ((jy - jx) + (Fy - Fx)) * twelfth;
+        const T Dx = (ex + Fx) * third, Dy = (ey + Fy) * third;
+        const T Da = ((ex + ey) + (Fx + Fy)) * twelfth;
+        const T Db = ((ey - ex) + (Fy - Fx)) * twelfth;
         o1 = Sx + Dx; o5 = Sx - Dx;
         o3 = Sy + Dy; o7 = Sy - Dy;
         o2 = Sa + Da; o6 = Sa - Da;
         o4 = Sb + Db; o8 = Sb - Db;
     } else {
         const T w = C.omega, m = T(1) - C.omega;
-        const T Dx = jx * third, Dy = jy * third;
-        const T Da = (jx + jy) * twelfth, Db = (jy - jx) * twelfth;
+        const T Dx = ex * third, Dy = ey * third;
+        const T Da = (ex + ey) * twelfth, Db = (ey - ex) * twelfth;
         const T Qx = Fx * third, Qy = Fy * third;
         const T Qa = (Fx + Fy) * twelfth, Qb = (Fy - Fx) * twelfth;
-        o1 = m * f[1] + w * (Sx + Dx) + Qx;
-        o5 = m * f[5] + w * (Sx - Dx) - Qx;
-        o3 = m * f[3] + w * (Sy + Dy) + Qy;
-        o7 = m * f[7] + w * (Sy - Dy) - Qy;
-        o2 = m * f[2] + w * (Sa + Da) + Qa;
-        o6 = m * f[6] + w * (Sa - Da) - Qa;
-        o4 = m * f[4] + w * (Sb + Db) + Qb;
-        o8 = m * f[8] + w * (Sb - Db) - Qb;
+        o1 = m * f[1] + w * (Sx + Dx) + (Tx + Qx);
+        o5 = m * f[5] + w * (Sx - Dx) + (Tx - Qx);
+        o3 = m * f[3] + w * (Sy + Dy) + (Ty + Qy);
+        o7 = m * f[7] + w * (Sy - Dy) + (Ty - Qy);
+        o2 = m * f[2] + w * (Sa + Da) + (Ta + Qa);
+        o6 = m * f[6] + w * (Sa - Da) + (Ta - Qa);
+        o4 = m * f[4] + w * (Sb + Db) + (Tb + Qb);
+        o8 = m * f[8] + w * (Sb - Db) + (Tb - Qb);
     }
     // In 16-bit storage, round the moving populations to what the readers
     // will reconstruct before the rest population is formed (f_1 possibly

@@ -167,40 +167,77 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
     // Eqs. (force), (forcefric), (alphafric): nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
     const float2 den = pfma(h, pfma(pk(2.0f), h, pk(6.0f * C.delta)), pk(3.0f * C.delta * C.delta));
     const float2 fr = make_float2(__fdividef(C.nu6, den.x), __fdividef(C.nu6, den.y));
-    const float2 Fx = psub(pmul(h, psub(pk(C.gx), gpx)), pmul(fr, jx));
-    const float2 Fy = psub(pmul(h, psub(pk(C.gy), gpy)), pmul(fr, jy));
+    // Eq. (LBE) as printed: u = j/h.  Second-order forcing (C.forcing):
+    // u (h + nu alpha/2) = j + F'/2 and the equilibria use h u for j (see
+    // collide_store)
+    float2 Fx, Fy, ux, uy, ex, ey;
+    if (C.forcing) {
+        const float2 fpx = pmul(h, psub(pk(C.gx), gpx)), fpy = pmul(h, psub(pk(C.gy), gpy));
+        const float2 d = pfma(pk(0.5f), fr, pk(1.0f));
+        const float2 q = make_float2(__fdividef(ih.x, d.x), __fdividef(ih.y, d.y));
+        ux = pmul(pfma(pk(0.5f), fpx, jx), q);
+        uy = pmul(pfma(pk(0.5f), fpy, jy), q);
+        ex = pmul(h, ux);
+        ey = pmul(h, uy);
+        Fx = psub(fpx, pmul(fr, ex));
+        Fy = psub(fpy, pmul(fr, ey));
+    } else {
+        Fx = psub(pmul(h, psub(pk(C.gx), gpx)), pmul(fr, jx));
+        Fy = psub(pmul(h, psub(pk(C.gy), gpy)), pmul(fr, jy));
+        ux = pmul(jx, ih);
+        uy = pmul(jy, ih);
+        ex = jx;
+        ey = jy;
+    }
     // Eq. (equilibria) with e^2 = 1 as S +- D per opposite pair; source 3 w_l c_l . F
-    const float2 ux = pmul(jx, ih), uy = pmul(jy, ih);
     const float2 A = pmul(pmul(h, psub(pmul(pk(C.g), h), pfma(ux, ux, pmul(uy, uy)))), pk(1.0f / 6.0f));
-    const float2 Sx = pfma(pk(0.5f), pmul(jx, ux), A);
-    const float2 Sy = pfma(pk(0.5f), pmul(jy, uy), A);
+    float2 Sx = pfma(pk(0.5f), pmul(ex, ux), A);
+    float2 Sy = pfma(pk(0.5f), pmul(ey, uy), A);
     const float2 a = padd(ux, uy), b = psub(uy, ux);
-    const float2 Sa = pmul(pfma(pk(0.5f), pmul(h, pmul(a, a)), A), pk(0.25f));
-    const float2 Sb = pmul(pfma(pk(0.5f), pmul(h, pmul(b, b)), A), pk(0.25f));
+    float2 Sa = pmul(pfma(pk(0.5f), pmul(h, pmul(a, a)), A), pk(0.25f));
+    float2 Sb = pmul(pfma(pk(0.5f), pmul(h, pmul(b, b)), A), pk(0.25f));
+    // second-order source: odd part scaled by (1 - omega/2), even part T
+    float2 Tx = pk(0.0f), Ty = pk(0.0f), Ta = pk(0.0f), Tb = pk(0.0f);
+    if (C.forcing) {
+        const float2 ks = pk(1.0f - 0.5f * C.omega);
+        Fx = pmul(Fx, ks);
+        Fy = pmul(Fy, ks);
+        const float2 uF3 = pmul(pfma(ux, Fx, pmul(uy, Fy)), pk(1.0f / 3.0f));
+        Tx = psub(pmul(ux, Fx), uF3);
+        Ty = psub(pmul(uy, Fy), uF3);
+        Ta = pmul(psub(pmul(a, padd(Fx, Fy)), uF3), pk(0.25f));
+        Tb = pmul(psub(pmul(b, psub(Fy, Fx)), uF3), pk(0.25f));
+        if constexpr (OMEGA1) {
+            Sx = padd(Sx, Tx);
+            Sy = padd(Sy, Ty);
+            Sa = padd(Sa, Ta);
+            Sb = padd(Sb, Tb);
+        }
+    }
     float2 o1, o2, o3, o4, o5, o6, o7, o8;
     if constexpr (OMEGA1) {
-        const float2 Dx = pmul(padd(jx, Fx), pk(1.0f / 3.0f));
-        const float2 Dy = pmul(padd(jy, Fy), pk(1.0f / 3.0f));
-        const float2 Da = pmul(padd(padd(jx, jy), padd(Fx, Fy)), pk(1.0f / 12.0f));
-        const float2 Db = pmul(padd(psub(jy, jx), psub(Fy, Fx)), pk(1.0f / 12.0f));
+        const float2 Dx = pmul(padd(ex, Fx), pk(1.0f / 3.0f));
+        const float2 Dy = pmul(padd(ey, Fy), pk(1.0f / 3.0f));
+        const float2 Da = pmul(padd(padd(ex, ey), padd(Fx, Fy)), pk(1.0f / 12.0f));
+        const float2 Db = pmul(padd(psub(ey, ex), psub(Fy, Fx)), pk(1.0f / 12.0f));
         o1 = padd(Sx, Dx); o5 = psub(Sx, Dx);
         o3 = padd(Sy, Dy); o7 = psub(Sy, Dy);
         o2 = padd(Sa, Da); o6 = psub(Sa, Da);
         o4 = padd(Sb, Db); o8 = psub(Sb, Db);
     } else {
         const float2 w = pk(C.omega), m = pk(1.0f - C.omega);
-        const float2 Dx = pmul(jx, pk(1.0f / 3.0f)), Dy = pmul(jy, pk(1.0f / 3.0f));
-        const float2 Da = pmul(padd(jx, jy), pk(1.0f / 12.0f)), Db = pmul(psub(jy, jx), pk(1.0f / 12.0f));
+        const float2 Dx = pmul(ex, pk(1.0f / 3.0f)), Dy = pmul(ey, pk(1.0f / 3.0f));
+        const float2 Da = pmul(padd(ex, ey), pk(1.0f / 12.0f)), Db = pmul(psub(ey, ex), pk(1.0f / 12.0f));
         const float2 Qx = pmul(Fx, pk(1.0f / 3.0f)), Qy = pmul(Fy, pk(1.0f / 3.0f));
         const float2 Qa = pmul(padd(Fx, Fy), pk(1.0f / 12.0f)), Qb = pmul(psub(Fy, Fx), pk(1.0f / 12.0f));
-        o1 = padd(pfma(m, f[0 * fstride], pmul(w, padd(Sx, Dx))), Qx);
-        o5 = psub(pfma(m, f[4 * fstride], pmul(w, psub(Sx, Dx))), Qx);
-        o3 = padd(pfma(m, f[2 * fstride], pmul(w, padd(Sy, Dy))), Qy);
-        o7 = psub(pfma(m, f[6 * fstride], pmul(w, psub(Sy, Dy))), Qy);
-        o2 = padd(pfma(m, f[1 * fstride], pmul(w, padd(Sa, Da))), Qa);
-        o6 = psub(pfma(m, f[5 * fstride], pmul(w, psub(Sa, Da))), Qa);
-        o4 = padd(pfma(m, f[3 * fstride], pmul(w, padd(Sb, Db))), Qb);
-        o8 = psub(pfma(m, f[7 * fstride], pmul(w, psub(Sb, Db))), Qb);
+        o1 = padd(pfma(m, f[0 * fstride], pmul(w, padd(Sx, Dx))), padd(Tx, Qx));
+        o5 = padd(pfma(m, f[4 * fstride], pmul(w, psub(Sx, Dx))), psub(Tx, Qx));
+        o3 = padd(pfma(m, f[2 * fstride], pmul(w, padd(Sy, Dy))), padd(Ty, Qy));
+        o7 = padd(pfma(m, f[6 * fstride], pmul(w, psub(Sy, Dy))), psub(Ty, Qy));
+        o2 = padd(pfma(m, f[1 * fstride], pmul(w, padd(Sa, Da))), padd(Ta, Qa));
+        o6 = padd(pfma(m, f[5 * fstride], pmul(w, psub(Sa, Da))), psub(Ta, Qa));
+        o4 = padd(pfma(m, f[3 * fstride], pmul(w, padd(Sb, Db))), padd(Tb, Qb));
+        o8 = padd(pfma(m, f[7 * fstride], pmul(w, psub(Sb, Db))), psub(Tb, Qb));
     }
     // stored rest population f*_0 - href = (h - href) - sum_{l>0} f*_l, with
     // the exact residuals folded back as in collide_store

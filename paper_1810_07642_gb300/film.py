@@ -18,9 +18,9 @@ _DT = {"f32": (L.TF_LBM_F32, torch.float32), "f64": (L.TF_LBM_F64, torch.float64
 
 def make_params(nx, ny, dtype="f32", tau=1.0, gamma=0.01, g=0.0, delta=1.0, hstar=0.07,
                 n_exp=3, m_exp=2, pi_sign=1, gx_body=0.0, gy_body=0.0, theta_uniform=0.0,
-                **_ignored) -> L.Params:
+                forcing=0, **_ignored) -> L.Params:
     code = _DT[dtype][0]
-    return L.Params(int(nx), int(ny), code, int(n_exp), int(m_exp), int(pi_sign), float(tau),
+    return L.Params(int(nx), int(ny), code, int(n_exp), int(m_exp), int(pi_sign), int(forcing), float(tau),
                     float(gamma), float(g), float(delta), float(hstar), float(gx_body),
                     float(gy_body), float(theta_uniform))
 

@@ -50,11 +50,29 @@ def test_binding_covers_header(libpath):
         assert callable(getattr(L, name))
 
 
-def test_struct_mirrors_match_header_layout():
-    # 6 int32 then 8 doubles; 4 int32
-    assert ctypes.sizeof(L.Params) == 6 * 4 + 8 * 8
-    assert L.Params.tau.offset == 24
-    assert ctypes.sizeof(L.Launch) == 16
+def test_struct_mirrors_match_header_layout(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler
+    gives the structs of include/tflbm.h."""
+    import subprocess
+    structs = {"tf_lbm_params": L.Params, "tf_lbm_launch": L.Launch,
+               "tf_lbm_batch_launch": L.BatchLaunch}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tflbm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (l.split() for l in out if l.strip())}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_library_loads_without_gpu_and_reports_version(libpath):

@@ -256,3 +256,22 @@ def test_tape_gradient_random_configurations(case):
     assert abs(loss.item() - L_o) <= 1e-11 * abs(L_o)
     assert np.abs(theta.grad.cpu().numpy() - gth_o).max() <= 1e-9 * np.abs(gth_o).max()
     assert np.abs(hh.grad.cpu().numpy() - gh0_o).max() <= 1e-9 * np.abs(gh0_o).max()
+
+
+def test_adjoint_rejects_second_order_forcing():
+    """The hand-written adjoint differentiates Eq. (LBE) as printed; the
+    second-order-forcing reading is refused, not silently differentiated
+    as the other scheme."""
+    h0, th, p = inputs.small_random(16, 12, seed=1)
+    sim = ThinFilm(dict(p, forcing=1), h0, th, dtype="f64")
+    f = sim.get_state()
+    a = torch.zeros_like(f)
+    gk = torch.zeros((12, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.TfLbmError) as e:
+        L.tf_lbm_adjoint_step(sim.handle, f.data_ptr(), a.data_ptr(), torch.empty_like(f).data_ptr(),
+                              gk.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == L.TF_LBM_ERR_UNSUPPORTED
+    with pytest.raises(L.TfLbmError) as e:
+        L.tf_lbm_tape_create(sim.handle, sim.h0_dev.data_ptr(), sim.theta_dev.data_ptr(), 10, 0)
+    assert e.value.code == L.TF_LBM_ERR_UNSUPPORTED
+    sim.close()
