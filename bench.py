@@ -36,17 +36,25 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS (D2Q9 thin-film step) and % of HBM roofline; adjoint/forward cost ratio"
 N_SIDE = 2048
 BYTES_PER_LU = 76  # FP32: 9 populations read + 9 written + kappa(x)
-PROFILE = os.path.join(ROOT, "profiles", "k_step_f32_patterned_2048.txt")
-KERNEL_SOURCES = ["paper_1810_07642_gb300/csrc/tflbm_step.cuh",
-                  "paper_1810_07642_gb300/csrc/step_f32.cu"]
+_CSRC = "paper_1810_07642_gb300/csrc/"
+# committed ncu summary of the default step kernel of each storage form and
+# the sources that kernel is compiled from (the summary's kernel_hash)
+PROFILES = {
+    "f32": ("k_step_f32_patterned_2048.txt",
+            [_CSRC + "tflbm_step.cuh", _CSRC + "step_f32.cu", _CSRC + "tflbm_internal.h"]),
+    "f16": ("k_step2_f16_patterned_2048.txt",
+            [_CSRC + "tflbm_step.cuh", _CSRC + "tflbm_step2.cuh", _CSRC + "step2_f16.cu",
+             _CSRC + "tflbm_internal.h"]),
+}
 WORKLOAD = ("chemically patterned dewetting, 2048x2048 periodic D2Q9 thin film, FP32 "
             "populations; h0=1+U(-1e-2,1e-2); theta stripes period 256 (10/40 deg) + 32 "
             "seeded discs (10 deg); gamma=0.01, h*=0.07, (n,m)=(3,2), tau=1, delta=1, g=0")
 
 
-def kernel_hash() -> str:
+def kernel_hash(storage: str = "f32") -> str:
+    """Hash of the sources of the default step kernel for one storage form."""
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in PROFILES[storage][1]:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -61,18 +69,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic():
+def profiled_traffic(storage: str = "f32"):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary
     (lines "key: value"), if it was taken on the current kernel source."""
-    if not os.path.exists(PROFILE):
+    if storage not in PROFILES:
+        return None, None
+    path = os.path.join(ROOT, "profiles", PROFILES[storage][0])
+    if not os.path.exists(path):
         return None, None
     d = {}
-    with open(PROFILE) as fh:
+    with open(path) as fh:
         for line in fh:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("kernel_hash") != kernel_hash() or "dram_bytes_per_launch" not in d:
+    if d.get("kernel_hash") != kernel_hash(storage) or "dram_bytes_per_launch" not in d:
         return None, d
     return float(d["dram_bytes_per_launch"]), d
 
@@ -674,7 +685,7 @@ def run_tflbm(args):
     bpl = BYTES_PER_LU if args.storage == "f32" else 44  # 16-bit: 2 x (4 + 8 x 2) + 4
     achieved = bpl * nodes / kern_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic, prof = profiled_traffic() if args.storage == "f32" else (None, None)
+    traffic, prof = profiled_traffic(args.storage)
 
     # end to end through the public API with host buffers (pinned)
     h_host = torch.from_numpy(np.asarray(h0, np.float32)).pin_memory()
