@@ -187,13 +187,15 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.status = H->status;
     C.wait_limit = H->wait_limit;
     C.forcing = H->p.forcing;
+    C.flip = 0;
     return C;
 }
 
 cudaError_t launch_one_step(tf_lbm_handle* H, int from, cudaStream_t st)
 {
-    const Consts<float> c32 = make_consts<float>(H);
-    const Consts<double> c64 = make_consts<double>(H);
+    Consts<float> c32 = make_consts<float>(H);
+    Consts<double> c64 = make_consts<double>(H);
+    c32.flip = c64.flip = from & 1;
     return launch_step(H->desc.store, H->buf[from], H->buf[from ^ 1], H->kappa, H->G, &c32, &c64,
                        H->shape, st);
 }

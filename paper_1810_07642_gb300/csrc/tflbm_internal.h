@@ -76,6 +76,7 @@ struct Consts {
     int* status;     // device word for kStatusTimeout (may be null)
     int wait_limit;  // polls of one mbarrier before giving up (<= 0: give up at once)
     int forcing;     // 0: Eq. (LBE) as printed; 1: second-order forcing
+    int flip;        // 0 / 1, alternating from step to step: reverses every band's march
 };
 
 // Launch shape of the fused step.

@@ -376,7 +376,7 @@ struct Band {
 };
 
 template <int BX>
-__device__ __forceinline__ Band make_band(const Geom& G, int t, int strip, int band, int nbands)
+__device__ __forceinline__ Band make_band(const Geom& G, int t, int strip, int band, int nbands, int flip)
 {
     Band b;
     constexpr int W = BX - 4;
@@ -392,7 +392,9 @@ __device__ __forceinline__ Band make_band(const Geom& G, int t, int strip, int b
     // the start or both at the end of the kernel) and the second read hits
     // L2.  March step k forms h of row r(k) = rstart + k dir, the pressure of
     // row r(k-1) and collides row r(k-3), for k = 0 .. R+4.
-    b.dir = (band & 1) ? -1 : 1;
+    // Every other step (flip) all bands reverse, so a band starts on the rows
+    // it wrote last, which are still in L2.
+    b.dir = ((band + flip) & 1) ? -1 : 1;
     b.R = b.yend - b.ybeg;
     b.rstart = b.dir > 0 ? b.ybeg - 2 : b.yend + 1;
     return b;
@@ -433,7 +435,7 @@ __device__ __forceinline__ void step_band(const T* __restrict__ fin0, const SM* 
     __shared__ T stg[ASYNC ? kAsyncStages : 1][9][ASYNC ? BX : 1];
     const int t = threadIdx.x;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
-    const Band B = make_band<BX>(G, t, strip, band, nbands);
+    const Band B = make_band<BX>(G, t, strip, band, nbands, C.flip);
     const bool disj = KFIELD || C.kappa_u != T(0);
     const int dir = B.dir, R = B.R;
 
@@ -608,7 +610,8 @@ __device__ __forceinline__ void batch_item(const BatchItem it, const BatchDomain
 {
     const BatchDomain<T>& D = doms[it.dom];
     const Geom G = D.G;
-    const Consts<T> C = D.C;
+    Consts<T> C = D.C;
+    C.flip = parity;
     const void* fin = D.buf[parity];
     void* fout = D.buf[parity ^ 1];
     const T* f0 = (const T*)fin;
@@ -770,7 +773,7 @@ k_step_tma(const T* __restrict__ fin0, const SM* __restrict__ finm, T* __restric
 
     const int t = threadIdx.x;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
-    const Band B = make_band<BX>(G, t, blockIdx.x, blockIdx.y, gridDim.y);
+    const Band B = make_band<BX>(G, t, blockIdx.x, blockIdx.y, gridDim.y, C.flip);
     const bool disj = KFIELD || C.kappa_u != T(0);
     const int dir = B.dir, R = B.R;
     const int x = wrap_index(B.x0 - 2 + t, nx);

@@ -325,7 +325,7 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     const bool ocol = t >= 1 && 2 * t <= weff;
     const int ybeg = (int)(((long long)band * ny) / nbands);
     const int yend = (int)(((long long)(band + 1) * ny) / nbands);
-    const int dir = (band & 1) ? -1 : 1;
+    const int dir = ((band + C.flip) & 1) ? -1 : 1;  // reversed every other step (see make_band)
     const int R = yend - ybeg;
     const int rstart = dir > 0 ? ybeg - 2 : yend + 1;
     const bool disj = KFIELD || C.kappa_u != 0.0f;
