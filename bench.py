@@ -40,8 +40,9 @@ _CSRC = "paper_1810_07642_gb300/csrc/"
 # committed ncu summary of the default step kernel of each storage form and
 # the sources that kernel is compiled from (the summary's kernel_hash)
 PROFILES = {
-    "f32": ("k_step_f32_patterned_2048.txt",
-            [_CSRC + "tflbm_step.cuh", _CSRC + "step_f32.cu", _CSRC + "tflbm_internal.h"]),
+    "f32": ("k_step2_f32_patterned_2048.txt",
+            [_CSRC + "tflbm_step.cuh", _CSRC + "tflbm_step2.cuh", _CSRC + "step2_f32.cu",
+             _CSRC + "tflbm_internal.h"]),
     "f16": ("k_step2_f16_patterned_2048.txt",
             [_CSRC + "tflbm_step.cuh", _CSRC + "tflbm_step2.cuh", _CSRC + "step2_f16.cu",
              _CSRC + "tflbm_internal.h"]),

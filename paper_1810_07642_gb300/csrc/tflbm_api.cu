@@ -106,27 +106,30 @@ int store_of(int dtype)
     }
 }
 
-// Default launch shape: the two-column kernel where it applies, CTAs 128
-// columns wide (one-column kernel on lattices narrower than 1024: 64), and
+// Default launch shape: the two-column kernel where it applies (CTAs 64
+// columns wide for 16-bit storage, 128 for FP32), else the one-column kernel
+// with CTAs 128 columns wide (64 on lattices narrower than 1024), and
 // a band height that makes the grid one full wave of
 // resident CTAs (all bands do the same work, so a partial second wave would
 // idle most SMs), but no shorter than 16 rows: each band spends 5 warm-up rows.
 Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 {
     Shape s;
-    // two columns per thread where pairs fit (nx even) for 16-bit storage:
-    // it issues fewer instructions per node than the one-column kernel, whose
-    // decode and encode work makes it issue bound; FP32 storage keeps the
-    // one-column kernel, which measured faster
+    // two columns per thread where pairs fit (nx even): it issues fewer
+    // instructions per node than the one-column kernel, which is issue bound.
+    // 16-bit storage uses it at 64 columns per CTA (one warp), FP32 at 128;
+    // FP32 at tau != 1 keeps the one-column kernel (its pulled-population ring
+    // costs the two-column kernel resident warps)
     const int store = store_of(p.dtype);
-    const bool pair = pair_pipeline_ok(G.nx, store) && (store == kStoreF16 || store == kStoreBF16);
-    s.block_x = (pair || G.nx >= 1024) ? 128 : 64;
+    const bool om1 = p.tau == 1.0;
+    const bool narrow = store == kStoreF16 || store == kStoreBF16;
+    const bool pair = pair_pipeline_ok(G.nx, store) && (narrow || (store == kStoreF32 && om1));
+    s.block_x = pair ? (narrow ? 64 : 128) : (G.nx >= 1024 ? 128 : 64);
     const int strips = (G.nx + s.block_x - 5) / (s.block_x - 4);  // CTAs overlap by 4 columns
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const bool om1 = p.tau == 1.0;
     // otherwise per-thread loads: measured faster than the bulk-copy pipeline
     // on GB300 once loads are prefetched a row ahead
     s.pipeline = pair ? kPipePair : kPipeLdg;
@@ -182,6 +185,7 @@ Consts<T> make_consts(const tf_lbm_handle* H)
     C.r_diag = T(H->desc.r_diag);
     C.nr_axis = T(-H->desc.r_axis * H->desc.mscale);
     C.nr_diag = T(-H->desc.r_diag * H->desc.mscale);
+    C.r_sum = T(4.0 * (H->desc.r_axis + H->desc.r_diag));
     C.n_exp = H->p.n_exp;
     C.m_exp = H->p.m_exp;
     C.status = H->status;

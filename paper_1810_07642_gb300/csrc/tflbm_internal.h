@@ -72,6 +72,7 @@ struct Consts {
     // R_l = f_eq_l(href, 0) = r_axis (odd l) or r_diag (even l); minv = 1/mscale
     T mscale, minv, r_axis, r_diag;
     T nr_axis, nr_diag;  // -r_axis * mscale, -r_diag * mscale (exact: mscale is a power of 2)
+    T r_sum;             // sum over the eight moving directions of R_l = 4 (r_axis + r_diag)
     int n_exp, m_exp;
     int* status;     // device word for kStatusTimeout (may be null)
     int wait_limit;  // polls of one mbarrier before giving up (<= 0: give up at once)

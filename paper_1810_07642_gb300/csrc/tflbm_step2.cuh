@@ -5,27 +5,42 @@
 //
 // Why: the one-column kernel issues about ten warp instructions per node and
 // is limited by instruction issue, not by HBM.  Two columns per thread halve
-// the per-node cost of addressing, loop control, shared-memory traffic and
-// barriers, turn every population load and store into one aligned 8-byte
-// (FP32) or 4-byte (16-bit pair) access, and let the node arithmetic run on
-// Blackwell's paired FP32 instructions (two lanes of float math per issued
-// instruction).
+// the per-node cost of addressing, loop control and barriers, turn every
+// population load and store into one aligned 8-byte (FP32) or 4-byte (16-bit
+// pair) access, and let the node arithmetic run on Blackwell's paired FP32
+// instructions (two lanes of float math per issued instruction).
+//
+// Storage units.  16-bit storage keeps v_l = (f_l - R_l) * scale for the
+// moving populations (R_l the rest equilibrium at href, scale a power of 2).
+// The kernel computes on v_l as decoded (one conversion, no arithmetic):
+// sums of moving populations need the R_l only through their total 4 (R_axis
+// + R_diag), momenta not at all (the R_l are symmetric), and the collision
+// forms (f*_l - R_l) * scale directly, with scale and R_l folded into its
+// constants.  FP32 storage is the case scale = 1, R_l = 0.
 //
 // Streaming without misaligned loads.  Thread t loads the nine planes at its
 // own aligned column pair (c, c+1).  Populations with c_x = 0 arrive from the
 // same columns.  Those with c_x = +1 (l = 1, 2, 8) arrive from the column to
 // the left and those with c_x = -1 (l = 4, 5, 6) from the right, so only one
-// value per direction crosses a pair boundary; it comes from the neighbouring
-// lane by a warp shuffle.  At tau = 1 only their sums matter (the collision
-// needs h and j alone), so per row four shuffles move the partial sums
-// R = f1 + f2 + f8, L = f4 + f5 + f6 and their y-momenta.  Lane 0 and lane 31
-// of every warp read the three planes of their outer neighbour column
-// themselves (predicated loads that hit L1/L2).
+// value per direction crosses a pair boundary.  At tau = 1 the collision
+// needs h and j alone, so each thread first sums the three c_x = +1 and the
+// three c_x = -1 populations of its own columns; per row four warp shuffles
+// then move those two sums and their y-momenta across the pair boundary
+// (general tau: six shuffles of the single values, which the relaxation
+// needs).  Lane 0 and lane 31 of every warp read the three elements of their
+// outer neighbour column themselves (predicated loads that hit L1/L2).
 //
-// Rows, bands, shared rings, the reference-height storage and the exact mass
-// folding are those of step_band (tflbm_step.cuh).  Needs nx even (pairs
-// never straddle the periodic seam); compute type FP32, storage FP32, FP16 or
-// BF16.
+// Stencils.  The h and p rows live in 4-row shared rings at their own
+// columns; a thread reads its pair as one aligned 8-byte load and the two
+// outer neighbours as single values.  (A second, column-shifted copy of each
+// row, which would make the shifted pairs aligned loads too, measured slower:
+// its extra stores and shared memory cost more than the register moves they
+// save.)
+//
+// Rows, bands, march direction, the reference-height storage and the exact
+// mass folding are those of step_band (tflbm_step.cuh).  Needs nx even
+// (pairs never straddle the periodic seam); compute type FP32, storage FP32,
+// FP16 or BF16.
 #pragma once
 #include "tflbm_step.cuh"
 
@@ -47,23 +62,27 @@ __device__ __forceinline__ void ptwo_sum(float2 a, float2 b, float2& s, float2& 
 }
 
 // ---- pair storage of the moving populations --------------------------------
-// V is one aligned pair of stored values; dec gives the two stored values as
-// floats, enc rounds two floats to the storage type.
+// V is one aligned pair of stored values; dec gives them as floats in storage
+// units (exact), enc rounds two floats to the storage type, dec1 converts one
+// stored element.
 template <typename SM> struct PairIO;
 template <> struct PairIO<float> {
     using V = float2;
     static __device__ __forceinline__ float2 dec(float2 q) { return q; }
     static __device__ __forceinline__ float2 enc(float2 v) { return v; }
+    static __device__ __forceinline__ float dec1(float q) { return q; }
 };
 template <> struct PairIO<__half> {
     using V = __half2;
     static __device__ __forceinline__ float2 dec(__half2 q) { return __half22float2(q); }
     static __device__ __forceinline__ __half2 enc(float2 v) { return __float22half2_rn(v); }
+    static __device__ __forceinline__ float dec1(__half q) { return __half2float(q); }
 };
 template <> struct PairIO<__nv_bfloat16> {
     using V = __nv_bfloat162;
     static __device__ __forceinline__ float2 dec(__nv_bfloat162 q) { return __bfloat1622float2(q); }
     static __device__ __forceinline__ __nv_bfloat162 enc(float2 v) { return __float22bfloat162_rn(v); }
+    static __device__ __forceinline__ float dec1(__nv_bfloat16 q) { return __bfloat162float(q); }
 };
 
 template <typename V> __device__ __forceinline__ V ldpair(const V* p) { return __ldg(p); }
@@ -80,56 +99,37 @@ template <typename V> __device__ __forceinline__ V from_bits(uint32_t u)
     memcpy(&v, &u, 4);
     return v;
 }
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// Stored pair -> population values (16-bit: q / scale + R_l, one fma each).
-template <typename SM>
-__device__ __forceinline__ float2 decode_pair(typename PairIO<SM>::V q, float R, const Consts<float>& C)
+// The nine pairs of one 3 x 4 stencil window of a shared row triple: for
+// each of the rows n (+y), c, s (-y) the pair at the thread's own columns
+// (x, x+1) and the shifted pairs (x-1, x) and (x+1, x+2).
+struct Win {
+    float2 n0, nL, nR, c0, cL, cR, s0, sL, sR;
+};
+// rows n, c, s of a ring; j is the slot of the pair's first column
+__device__ __forceinline__ Win load_win(const float* rn, const float* rc, const float* rs, int j)
 {
-    if constexpr (std::is_same<SM, float>::value) return q;
-    else return pfma(PairIO<SM>::dec(q), pk(C.minv), pk(R));
+    Win w;
+    w.n0 = lds2(rn + j); w.nL = make_float2(rn[j - 1], w.n0.x); w.nR = make_float2(w.n0.y, rn[j + 2]);
+    w.c0 = lds2(rc + j); w.cL = make_float2(rc[j - 1], w.c0.x); w.cR = make_float2(w.c0.y, rc[j + 2]);
+    w.s0 = lds2(rs + j); w.sL = make_float2(rs[j - 1], w.s0.x); w.sR = make_float2(w.s0.y, rs[j + 2]);
+    return w;
 }
-
-// Population values -> stored pair, and o replaced by what readers decode.
-template <typename SM>
-__device__ __forceinline__ typename PairIO<SM>::V narrow_pair(float2& o, float R, float NR, const Consts<float>& C)
-{
-    const typename PairIO<SM>::V q = PairIO<SM>::enc(pfma(o, pk(C.mscale), pk(NR)));
-    o = pfma(PairIO<SM>::dec(q), pk(C.minv), pk(R));
-    return q;
-}
-
 
 // ---------------------------------------------------------------------------
-// Node arithmetic shared by both load paths.
+// Node arithmetic.
 
-// h - href, its pull-sum residual and j of the two nodes from their pulled
-// populations n[l-1] (l = 1..8) and f_0 - href.  The moving populations are
-// summed first (they are small), the last addition is error-free (see sum9).
-__device__ __forceinline__ void pair_moments(const float2 (&n)[8], float2 f0, float2& dh, float2& er,
-                                             float2& jx, float2& jy)
+// Film pressure (Eq. pfilm with Eq. disjoiningP) of the two nodes from the h
+// window; writes 1/h to ih.
+__device__ __forceinline__ float2 pair_pressure(const Win& H, float2 kap, bool disj, const Consts<float>& C,
+                                                float2& ih)
 {
-    const float2 rs = padd(padd(n[0], n[1]), n[7]);  // c_x = +1: l = 1, 2, 8
-    const float2 ls = padd(padd(n[4], n[3]), n[5]);  // c_x = -1: l = 5, 4, 6
-    ptwo_sum(f0, padd(padd(padd(n[2], n[6]), rs), ls), dh, er);
-    jx = psub(rs, ls);
-    jy = padd(padd(psub(n[2], n[6]), psub(n[1], n[7])), psub(n[3], n[5]));
-}
-
-// Film pressure (Eq. pfilm with Eq. disjoiningP) of the two nodes from the
-// shared h rows n (+y), c, s (-y) at the pair's slot; writes 1/h to ih.
-__device__ __forceinline__ float2 pair_pressure(const float* hn, const float* hc, const float* hs, float2 kap,
-                                                bool disj, const Consts<float>& C, float2& ih)
-{
-    const float2 c0 = *reinterpret_cast<const float2*>(hc);
-    const float2 n0 = *reinterpret_cast<const float2*>(hn);
-    const float2 s0 = *reinterpret_cast<const float2*>(hs);
-    const float cl = hc[-1], cr = hc[2], nl = hn[-1], nr = hn[2], sl = hs[-1], sr = hs[2];
     // Eq. (n_laplace): axis neighbours left + right + up + down, diagonal the four corners
-    const float2 axis = padd(padd(make_float2(cl, c0.x), make_float2(c0.y, cr)), padd(n0, s0));
-    const float2 diag = padd(padd(make_float2(nl, n0.x), make_float2(n0.y, nr)),
-                             padd(make_float2(sl, s0.x), make_float2(s0.y, sr)));
-    float2 lap = pmul(pfma(pk(4.0f), axis, pfma(pk(-20.0f), c0, diag)), pk(1.0f / 6.0f));
-    const float2 h = padd(c0, pk(C.href));
+    const float2 axis = padd(padd(H.cL, H.cR), padd(H.n0, H.s0));
+    const float2 diag = padd(padd(H.nL, H.nR), padd(H.sL, H.sR));
+    float2 lap = pmul(pfma(pk(4.0f), axis, pfma(pk(-20.0f), H.c0, diag)), pk(1.0f / 6.0f));
+    const float2 h = padd(H.c0, pk(C.href));
     ih = make_float2(__fdividef(1.0f, h.x), __fdividef(1.0f, h.y));
     if (disj) {
         const float2 r = pmul(pk(C.hstar), ih);
@@ -142,31 +142,30 @@ __device__ __forceinline__ float2 pair_pressure(const float* hn, const float* hc
 }
 
 // Force, collision and store of the two nodes (the arithmetic of
-// collide_store on both lanes).  pn, pc, ps: shared p rows o+1, o, o-1 at the
-// pair's slot; f: the pulled moving populations (omega != 1 only); i: the
-// storage offset of the pair's first column.
+// collide_store on both lanes, in storage units).  P: the p window around
+// the pair (n = row o+1, s = row o-1); f: the pulled moving populations in
+// storage units (omega != 1 only); i: the storage offset of the pair's first
+// column.
 template <typename SM, bool OMEGA1>
-__device__ __forceinline__ void pair_collide_store(const float* pn, const float* pc, const float* ps, float2 dh,
-                                                   float2 ih, float2 jx, float2 jy, float2 er,
-                                                   const float2* f, int fstride, float* __restrict__ fout0,
-                                                   SM* __restrict__ foutm, int i, int plane,
-                                                   const Consts<float>& C)
+__device__ __forceinline__ void pair_collide_store(const Win& P, float2 dh, float2 ih, float2 jx, float2 jy,
+                                                   float2 er, const float2* f, int fstride,
+                                                   float* __restrict__ fout0, SM* __restrict__ foutm, int i,
+                                                   int plane, const Consts<float>& C)
 {
-    using V = typename PairIO<SM>::V;
+    using IO = PairIO<SM>;
+    using V = typename IO::V;
     constexpr bool NARROW = !std::is_same<SM, float>::value;
-    const float2 n0 = *reinterpret_cast<const float2*>(pn);
-    const float2 c0 = *reinterpret_cast<const float2*>(pc);
-    const float2 s0 = *reinterpret_cast<const float2*>(ps);
-    const float2 nL = make_float2(pn[-1], n0.x), nR = make_float2(n0.y, pn[2]);
-    const float2 sL = make_float2(ps[-1], s0.x), sR = make_float2(s0.y, ps[2]);
-    const float2 cL = make_float2(pc[-1], c0.x), cR = make_float2(c0.y, pc[2]);
+    // storage scale (1 for FP32, a compile-time constant there)
+    const float ms = NARROW ? C.mscale : 1.0f;
     // Eq. (derivative): grad p = 3 sum_l w_l c_l p(x + c_l)
-    const float2 gpx = pfma(psub(cR, cL), pk(1.0f / 3.0f), pmul(padd(psub(nR, nL), psub(sR, sL)), pk(1.0f / 12.0f)));
-    const float2 gpy = pfma(psub(n0, s0), pk(1.0f / 3.0f), pmul(padd(psub(nR, sR), psub(nL, sL)), pk(1.0f / 12.0f)));
+    const float2 gpx = pfma(psub(P.cR, P.cL), pk(1.0f / 3.0f),
+                            pmul(padd(psub(P.nR, P.nL), psub(P.sR, P.sL)), pk(1.0f / 12.0f)));
+    const float2 gpy = pfma(psub(P.n0, P.s0), pk(1.0f / 3.0f),
+                            pmul(padd(psub(P.nR, P.sR), psub(P.nL, P.sL)), pk(1.0f / 12.0f)));
     const float2 h = padd(dh, pk(C.href));
     // Eqs. (force), (forcefric), (alphafric): nu alpha u = 6 nu j / (2h^2 + 6 delta h + 3 delta^2)
     const float2 den = pfma(h, pfma(pk(2.0f), h, pk(6.0f * C.delta)), pk(3.0f * C.delta * C.delta));
-    const float2 fr = make_float2(__fdividef(C.nu6, den.x), __fdividef(C.nu6, den.y));
+    const float2 fr = pmul(pk(C.nu6), make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y)));
     // Eq. (LBE) as printed: u = j/h.  Second-order forcing (C.forcing):
     // u (h + nu alpha/2) = j + F'/2 and the equilibria use h u for j (see
     // collide_store)
@@ -189,24 +188,29 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
         ex = jx;
         ey = jy;
     }
-    // Eq. (equilibria) with e^2 = 1 as S +- D per opposite pair; source 3 w_l c_l . F
-    const float2 A = pmul(pmul(h, psub(pmul(pk(C.g), h), pfma(ux, ux, pmul(uy, uy)))), pk(1.0f / 6.0f));
-    float2 Sx = pfma(pk(0.5f), pmul(ex, ux), A);
-    float2 Sy = pfma(pk(0.5f), pmul(ey, uy), A);
+    // Eq. (equilibria) with e^2 = 1 as S +- D per opposite pair, source
+    // 3 w_l c_l . F; in storage units S' = (S - R_l) ms, D' = D ms.
+    // A6 = 6 A = h (g h - u^2).
+    const float2 A6 = pmul(h, psub(pmul(pk(C.g), h), pfma(ux, ux, pmul(uy, uy))));
+    const float2 Aa = NARROW ? pfma(A6, pk(ms * (1.0f / 6.0f)), pk(C.nr_axis)) : pmul(A6, pk(1.0f / 6.0f));
+    const float2 Ad = NARROW ? pfma(A6, pk(ms * (1.0f / 24.0f)), pk(C.nr_diag)) : pmul(A6, pk(1.0f / 24.0f));
+    float2 Sx = pfma(pmul(ex, pk(0.5f * ms)), ux, Aa);
+    float2 Sy = pfma(pmul(ey, pk(0.5f * ms)), uy, Aa);
     const float2 a = padd(ux, uy), b = psub(uy, ux);
-    float2 Sa = pmul(pfma(pk(0.5f), pmul(h, pmul(a, a)), A), pk(0.25f));
-    float2 Sb = pmul(pfma(pk(0.5f), pmul(h, pmul(b, b)), A), pk(0.25f));
+    const float2 h8 = pmul(h, pk(0.125f * ms));
+    float2 Sa = pfma(pmul(h8, a), a, Ad);
+    float2 Sb = pfma(pmul(h8, b), b, Ad);
     // second-order source: odd part scaled by (1 - omega/2), even part T
     float2 Tx = pk(0.0f), Ty = pk(0.0f), Ta = pk(0.0f), Tb = pk(0.0f);
     if (C.forcing) {
         const float2 ks = pk(1.0f - 0.5f * C.omega);
         Fx = pmul(Fx, ks);
         Fy = pmul(Fy, ks);
-        const float2 uF3 = pmul(pfma(ux, Fx, pmul(uy, Fy)), pk(1.0f / 3.0f));
-        Tx = psub(pmul(ux, Fx), uF3);
-        Ty = psub(pmul(uy, Fy), uF3);
-        Ta = pmul(psub(pmul(a, padd(Fx, Fy)), uF3), pk(0.25f));
-        Tb = pmul(psub(pmul(b, psub(Fy, Fx)), uF3), pk(0.25f));
+        const float2 uF3 = pmul(pfma(ux, Fx, pmul(uy, Fy)), pk(ms * (1.0f / 3.0f)));
+        Tx = pfma(pmul(ux, Fx), pk(ms), make_float2(-uF3.x, -uF3.y));
+        Ty = pfma(pmul(uy, Fy), pk(ms), make_float2(-uF3.x, -uF3.y));
+        Ta = pmul(pfma(pmul(a, padd(Fx, Fy)), pk(ms), make_float2(-uF3.x, -uF3.y)), pk(0.25f));
+        Tb = pmul(pfma(pmul(b, psub(Fy, Fx)), pk(ms), make_float2(-uF3.x, -uF3.y)), pk(0.25f));
         if constexpr (OMEGA1) {
             Sx = padd(Sx, Tx);
             Sy = padd(Sy, Ty);
@@ -214,22 +218,23 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
             Sb = padd(Sb, Tb);
         }
     }
+    const float2 m3 = pk(ms * (1.0f / 3.0f)), m12 = pk(ms * (1.0f / 12.0f));
     float2 o1, o2, o3, o4, o5, o6, o7, o8;
     if constexpr (OMEGA1) {
-        const float2 Dx = pmul(padd(ex, Fx), pk(1.0f / 3.0f));
-        const float2 Dy = pmul(padd(ey, Fy), pk(1.0f / 3.0f));
-        const float2 Da = pmul(padd(padd(ex, ey), padd(Fx, Fy)), pk(1.0f / 12.0f));
-        const float2 Db = pmul(padd(psub(ey, ex), psub(Fy, Fx)), pk(1.0f / 12.0f));
+        const float2 Gx = padd(ex, Fx), Gy = padd(ey, Fy);
+        const float2 Dx = pmul(Gx, m3), Dy = pmul(Gy, m3);
+        const float2 Da = pmul(padd(Gx, Gy), m12), Db = pmul(psub(Gy, Gx), m12);
         o1 = padd(Sx, Dx); o5 = psub(Sx, Dx);
         o3 = padd(Sy, Dy); o7 = psub(Sy, Dy);
         o2 = padd(Sa, Da); o6 = psub(Sa, Da);
         o4 = padd(Sb, Db); o8 = psub(Sb, Db);
     } else {
+        // (1 - omega)(f_l - R_l) + omega (f_eq_l - R_l) + source, in storage units
         const float2 w = pk(C.omega), m = pk(1.0f - C.omega);
-        const float2 Dx = pmul(ex, pk(1.0f / 3.0f)), Dy = pmul(ey, pk(1.0f / 3.0f));
-        const float2 Da = pmul(padd(ex, ey), pk(1.0f / 12.0f)), Db = pmul(psub(ey, ex), pk(1.0f / 12.0f));
-        const float2 Qx = pmul(Fx, pk(1.0f / 3.0f)), Qy = pmul(Fy, pk(1.0f / 3.0f));
-        const float2 Qa = pmul(padd(Fx, Fy), pk(1.0f / 12.0f)), Qb = pmul(psub(Fy, Fx), pk(1.0f / 12.0f));
+        const float2 Dx = pmul(ex, m3), Dy = pmul(ey, m3);
+        const float2 Da = pmul(padd(ex, ey), m12), Db = pmul(psub(ey, ex), m12);
+        const float2 Qx = pmul(Fx, m3), Qy = pmul(Fy, m3);
+        const float2 Qa = pmul(padd(Fx, Fy), m12), Qb = pmul(psub(Fy, Fx), m12);
         o1 = padd(pfma(m, f[0 * fstride], pmul(w, padd(Sx, Dx))), padd(Tx, Qx));
         o5 = padd(pfma(m, f[4 * fstride], pmul(w, psub(Sx, Dx))), psub(Tx, Qx));
         o3 = padd(pfma(m, f[2 * fstride], pmul(w, padd(Sy, Dy))), padd(Ty, Qy));
@@ -257,29 +262,25 @@ __device__ __forceinline__ void pair_collide_store(const float* pn, const float*
         om[0] = o1; om[hp] = o2; om[2 * hp] = o3; om[3 * hp] = o4;
         om[4 * hp] = o5; om[5 * hp] = o6; om[6 * hp] = o7; om[7 * hp] = o8;
     } else {
-        const float Rax = C.r_axis, Rdg = C.r_diag, NRa = C.nr_axis, NRd = C.nr_diag;
-        const V q3 = narrow_pair<SM>(o3, Rax, NRa, C);
-        const V q5 = narrow_pair<SM>(o5, Rax, NRa, C);
-        const V q7 = narrow_pair<SM>(o7, Rax, NRa, C);
-        const V q2 = narrow_pair<SM>(o2, Rdg, NRd, C);
-        const V q4 = narrow_pair<SM>(o4, Rdg, NRd, C);
-        const V q6 = narrow_pair<SM>(o6, Rdg, NRd, C);
-        const V q8 = narrow_pair<SM>(o8, Rdg, NRd, C);
-        const float2 osum = padd(padd(padd(o1, o5), padd(o3, o7)), padd(padd(o2, o6), padd(o4, o8)));
+        const V q2 = IO::enc(o2), q3 = IO::enc(o3), q4 = IO::enc(o4), q5 = IO::enc(o5);
+        const V q6 = IO::enc(o6), q7 = IO::enc(o7), q8 = IO::enc(o8), q1r = IO::enc(o1);
+        // what the readers reconstruct of l = 2..8 (storage units, exact)
+        const float2 rest = padd(padd(padd(IO::dec(q2), IO::dec(q3)), padd(IO::dec(q4), IO::dec(q5))),
+                                 padd(padd(IO::dec(q6), IO::dec(q7)), IO::dec(q8)));
+        // the moving populations' total with f_1 unrounded and rounded
+        const float2 osum = pfma(padd(rest, o1), pk(C.minv), pk(C.r_sum));
+        const float2 osr = pfma(padd(rest, IO::dec(q1r)), pk(C.minv), pk(C.r_sum));
         // the last residual goes to the finer of the two roundings: the 16-bit
         // one of f_1 - R or the FP32 one of f_0 - href (see collide_store)
         constexpr float kRatio = std::is_same<SM, __half>::value ? 8192.0f : 65536.0f;
-        const bool lx = fabsf(o1.x - Rax) * kRatio < fabsf(dh.x - osum.x);
-        const bool ly = fabsf(o1.y - Rax) * kRatio < fabsf(dh.y - osum.y);
-        float2 o1r = o1;
-        const V q1r = narrow_pair<SM>(o1r, Rax, NRa, C);
-        const float2 adj = psub(o1r, o1);
-        const float2 os = make_float2(lx ? osum.x : osum.x + adj.x, ly ? osum.y : osum.y + adj.y);
+        const float kr = kRatio * C.minv;  // |f_1 - R| = |o1| / ms
+        const bool lx = fabsf(o1.x) * kr < fabsf(dh.x - osum.x);
+        const bool ly = fabsf(o1.y) * kr < fabsf(dh.y - osum.y);
+        const float2 os = make_float2(lx ? osum.x : osr.x, ly ? osum.y : osr.y);
         float2 o0v, e2, o0n, e3;
         ptwo_sum(dh, make_float2(-os.x, -os.y), o0v, e2);
         ptwo_sum(o0v, padd(er, e2), o0n, e3);
-        float2 o1l = padd(o1, e3);
-        const V q1l = narrow_pair<SM>(o1l, Rax, NRa, C);
+        const V q1l = IO::enc(pfma(e3, pk(ms), o1));
         const uint32_t mask = (lx ? 0x0000ffffu : 0u) | (ly ? 0xffff0000u : 0u);
         const V q1 = from_bits<V>((bits(q1l) & mask) | (bits(q1r) & ~mask));
         reinterpret_cast<float2*>(fout0)[ip] = o0n;
@@ -309,13 +310,16 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     constexpr int NC = 2 * BX;  // columns per CTA
     constexpr int W = NC - 4;   // output columns per CTA
     constexpr int OFF = 2;      // ring slot of local column j is OFF + j (keeps pairs 8-byte aligned)
-    __shared__ __align__(16) float hsm[4][NC + 4];  // h - href
-    __shared__ __align__(16) float psm[4][NC + 4];  // film pressure
+    constexpr int RW = NC + 4;  // ring row width
+    // h - href and the film pressure (slot OFF + j: local column j)
+    __shared__ __align__(16) float hsm[4][RW];
+    __shared__ __align__(16) float psm[4][RW];
     // general tau: the eight pulled moving populations of the last four rows
     __shared__ __align__(16) float2 fsm[OMEGA1 ? 1 : 4][8][OMEGA1 ? 1 : BX];
-    // per-thread ring of j_x, j_y, the pull-sum residual and 1/h of the last
-    // four rows (each thread reads back only its own slots)
-    __shared__ __align__(16) float2 rsm[4][4][BX];
+    // per-thread rings of (j_x, j_y), the pull-sum residual and 1/h of the
+    // last four rows (each thread reads back only its own slots)
+    __shared__ __align__(16) float4 rsj[4][BX];
+    __shared__ __align__(16) float2 rse[4][BX], rsi[4][BX];
 
     const int t = threadIdx.x, lane = t & 31;
     const int nx = G.nx, ny = G.ny, pitch = G.pitch, plane = (int)G.plane;
@@ -329,17 +333,18 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     const int R = yend - ybeg;
     const int rstart = dir > 0 ? ybeg - 2 : yend + 1;
     const bool disj = KFIELD || C.kappa_u != 0.0f;
-    const float Rax = C.r_axis, Rdg = C.r_diag;
     const int c = wrap_index(x0 - 2 + 2 * t, nx);  // own pair (even)
+    const int j2 = OFF + 2 * t;                    // ring slot of the pair
 
     const bool edge = lane == 0 || lane == 31;
-    const int ce = lane == 0 ? wrap_index(c - 2, nx) : (c + 2 == nx ? 0 : c + 2);
-    // moving planes (index l - 1) a warp-edge lane reads at its outer
-    // neighbour pair, from rows y, y-1, y+1: lane 0 needs l = 1, 2, 8
-    // (arriving from the left), lane 31 needs l = 5, 4, 6 (from the right)
-    const int e0 = (lane == 0 ? 0 : 4) * plane;
-    const int e1 = (lane == 0 ? 1 : 3) * plane;
-    const int e2 = (lane == 0 ? 7 : 5) * plane;
+    // the outer neighbour column: c - 1 for lane 0, c + 2 for lane 31
+    const int ce = lane == 0 ? (c == 0 ? nx - 1 : c - 1) : (c + 2 == nx ? 0 : c + 2);
+    // moving planes (index l - 1) a warp-edge lane reads at that column, from
+    // rows y, y-1, y+1: lane 0 needs l = 1, 2, 8 (arriving from the left),
+    // lane 31 needs l = 5, 4, 6 (from the right)
+    const int e0 = (lane == 0 ? 0 : 4) * plane + ce;
+    const int e1 = (lane == 0 ? 1 : 3) * plane + ce;
+    const int e2 = (lane == 0 ? 7 : 5) * plane + ce;
     const float2* __restrict__ f0p = reinterpret_cast<const float2*>(fin0);
     const V* __restrict__ fmp = reinterpret_cast<const V*>(finm);
     const int half = plane >> 1;  // pairs per plane (pitch is even)
@@ -348,14 +353,14 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     // otherwise cost resident warps)
     constexpr int PF = NARROW ? 2 : 1;
     float2 q0[PF];
-    V qm[PF][8], qe[PF][3];
+    V qm[PF][8];
+    SM qe[PF][3];
 
-    // wrapped rows r(k-1), r(k), r(k+1), r(k+2)
     // wrapped rows r(k-1) .. r(k+3)
     int wm1 = wrap_index(rstart - dir, ny), w0 = wrap_index(rstart, ny);
     int w1 = wrap_index(rstart + dir, ny), w2 = wrap_index(rstart + 2 * dir, ny);
     int w3 = wrap_index(rstart + 3 * dir, ny);
-    // the nine planes (and the edge planes) pulled into row w, into register set b
+    // the nine planes (and the edge elements) pulled into row w, into register set b
     auto load_row = [&](auto b_c, int wb, int w, int wa) {
         constexpr int b = decltype(b_c)::value;
         const int ys = dir > 0 ? wb : wa, yn = dir > 0 ? wa : wb;  // rows y-1, y+1
@@ -372,9 +377,11 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         qm[b][6] = ldpair(fmp + TFLBM_IDX(6 * half + in, m8, st));    // l = 7
         qm[b][7] = ldpair(fmp + TFLBM_IDX(7 * half + in, m8, st));    // l = 8
         if (edge) {
-            qe[b][0] = ldpair(fmp + TFLBM_IDX((e0 + w * pitch + ce) >> 1, m8, st));
-            qe[b][1] = ldpair(fmp + TFLBM_IDX((e1 + ys * pitch + ce) >> 1, m8, st));
-            qe[b][2] = ldpair(fmp + TFLBM_IDX((e2 + yn * pitch + ce) >> 1, m8, st));
+            const long long e8 = 8LL * plane;
+            qe[b][0] = ldro(finm + TFLBM_IDX(e0 + w * pitch, e8, st));
+            qe[b][1] = ldro(finm + TFLBM_IDX(e1 + ys * pitch, e8, st));
+            qe[b][2] = ldro(finm + TFLBM_IDX(e2 + yn * pitch, e8, st));
+            (void)e8;
         }
         (void)m8;
         (void)st;
@@ -388,9 +395,10 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
     if (KFIELD && pcol)
         kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)wm1 * nx + c) >> 1, npair, C.status)];
 
-    // ring slots no thread writes (outer halves of the edge columns' stencils)
-    if (t < 4) {
-        const int j = t < 2 ? t : NC + t;
+    // ring slots no thread writes: columns -1 and NC (outer halves of the
+    // edge columns' stencils)
+    if (t < 2) {
+        const int j = t == 0 ? OFF - 1 : OFF + NC;
 #pragma unroll
         for (int s = 0; s < 4; ++s) hsm[s][j] = psm[s][j] = 0.0f;
     }
@@ -403,40 +411,52 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
         const float2 kap = kap_n;                    // kappa of row r(k-1)
         // ---- (A) h, j of row r(k)
         if (k <= R + 3) {
-            float2 f0, n[8];  // f_0 - href and the moving populations arriving at the pair
-            {
-                constexpr int rb = s % PF;  // register set of row r(k)
-                f0 = q0[rb];
-                float2 v[8];
+            constexpr int rb = s % PF;  // register set of row r(k)
+            const float2 f0 = q0[rb];   // f_0 - href
+            float2 v[8];                // moving populations at the own columns, storage units
 #pragma unroll
-                for (int l = 0; l < 8; ++l) v[l] = decode_pair<SM>(qm[rb][l], (l & 1) ? Rdg : Rax, C);
-                float ex = 0.f, ey = 0.f, ez = 0.f;  // left column of lane 0 / right column of lane 31
-                if (edge) {
-                    const float2 a = decode_pair<SM>(qe[rb][0], Rax, C);  // l = 1 or 5: axis
-                    const float2 b = decode_pair<SM>(qe[rb][1], Rdg, C);  // l = 2 or 4: diagonal
-                    const float2 d = decode_pair<SM>(qe[rb][2], Rdg, C);  // l = 8 or 6: diagonal
-                    ex = lane == 0 ? a.y : a.x;
-                    ey = lane == 0 ? b.y : b.x;
-                    ez = lane == 0 ? d.y : d.x;
-                }
-                // the loads of row r(k+PF) go out before this row's arithmetic
-                if constexpr (PF == 2) {
-                    if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
-                } else {
-                    if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
-                }
-                if (KFIELD && pcol)
-                    kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)w0 * nx + c) >> 1, npair,
-                                                                              C.status)];
-                // l = 1, 2, 8 arrive from the left, l = 4, 5, 6 from the right
+            for (int l = 0; l < 8; ++l) v[l] = IO::dec(qm[rb][l]);
+            // the three crossing populations at the outer column (warp-edge lanes)
+            float ea = 0.f, eb = 0.f, ed = 0.f;
+            if (edge) {
+                ea = IO::dec1(qe[rb][0]);  // l = 1 or 5
+                eb = IO::dec1(qe[rb][1]);  // l = 2 or 4
+                ed = IO::dec1(qe[rb][2]);  // l = 8 or 6
+            }
+            // the loads of row r(k+PF) go out before this row's arithmetic
+            if constexpr (PF == 2) {
+                if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
+            } else {
+                if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
+            }
+            if (KFIELD && pcol)
+                kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)w0 * nx + c) >> 1, npair,
+                                                                          C.status)];
+            // Rs, Ls: sums of the populations arriving from the left (l = 1,
+            // 2, 8) and from the right (l = 4, 5, 6) at the two nodes; tot:
+            // all eight; jyr: their y momentum (storage units)
+            float2 Rs, Ls, tot, jyr;
+            if constexpr (OMEGA1) {
+                const float2 Pc = padd(padd(v[0], v[1]), v[7]), Py = psub(v[1], v[7]);
+                const float2 Qc = padd(padd(v[4], v[3]), v[5]), Qy = psub(v[3], v[5]);
+                float pl = __shfl_up_sync(0xffffffffu, Pc.y, 1), pyl = __shfl_up_sync(0xffffffffu, Py.y, 1);
+                float qr = __shfl_down_sync(0xffffffffu, Qc.x, 1), qyr = __shfl_down_sync(0xffffffffu, Qy.x, 1);
+                if (lane == 0) { pl = (ea + eb) + ed; pyl = eb - ed; }
+                if (lane == 31) { qr = (ea + eb) + ed; qyr = eb - ed; }
+                Rs = make_float2(pl, Pc.x);
+                Ls = make_float2(Qc.y, qr);
+                jyr = padd(psub(v[2], v[6]), padd(make_float2(pyl, Py.x), make_float2(Qy.y, qyr)));
+            } else {
+                // the single arriving values, kept for the relaxation
                 float u1 = __shfl_up_sync(0xffffffffu, v[0].y, 1);
                 float u2 = __shfl_up_sync(0xffffffffu, v[1].y, 1);
                 float u8 = __shfl_up_sync(0xffffffffu, v[7].y, 1);
                 float d5 = __shfl_down_sync(0xffffffffu, v[4].x, 1);
                 float d4 = __shfl_down_sync(0xffffffffu, v[3].x, 1);
                 float d6 = __shfl_down_sync(0xffffffffu, v[5].x, 1);
-                if (lane == 0) { u1 = ex; u2 = ey; u8 = ez; }
-                if (lane == 31) { d5 = ex; d4 = ey; d6 = ez; }
+                if (lane == 0) { u1 = ea; u2 = eb; u8 = ed; }
+                if (lane == 31) { d5 = ea; d4 = eb; d6 = ed; }
+                float2 n[8];
                 n[0] = make_float2(u1, v[0].x);
                 n[1] = make_float2(u2, v[1].x);
                 n[2] = v[2];
@@ -445,41 +465,54 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 n[5] = make_float2(v[5].y, d6);
                 n[6] = v[6];
                 n[7] = make_float2(u8, v[7].x);
-            }
-            float2 dh, er, jx, jy;
-            pair_moments(n, f0, dh, er, jx, jy);
-            *reinterpret_cast<float2*>(&hsm[s][OFF + 2 * t]) = dh;
-            rsm[s][0][t] = jx;
-            rsm[s][1][t] = jy;
-            rsm[s][2][t] = er;
-            if constexpr (!OMEGA1) {
+                Rs = padd(padd(n[0], n[1]), n[7]);
+                Ls = padd(padd(n[4], n[3]), n[5]);
+                jyr = padd(padd(psub(n[2], n[6]), psub(n[1], n[7])), psub(n[3], n[5]));
 #pragma unroll
                 for (int l = 0; l < 8; ++l) fsm[s][l][t] = n[l];
             }
+            tot = padd(padd(v[2], v[6]), padd(Rs, Ls));
+            // h - href: the moving total is small, the last addition is
+            // error-free (see sum9)
+            float2 dh, er, jx, jy;
+            if constexpr (NARROW) {
+                ptwo_sum(f0, pfma(tot, pk(C.minv), pk(C.r_sum)), dh, er);
+                jx = pmul(psub(Rs, Ls), pk(C.minv));
+                jy = pmul(jyr, pk(C.minv));
+            } else {
+                ptwo_sum(f0, tot, dh, er);
+                jx = psub(Rs, Ls);
+                jy = jyr;
+            }
+            TFLBM_CHECK(j2 >= OFF && j2 + 1 < RW, C.status);
+            *reinterpret_cast<float2*>(&hsm[s][j2]) = dh;
+            rsj[s][t] = make_float4(jx.x, jx.y, jy.x, jy.y);
+            rse[s][t] = er;
         }
         __syncthreads();
         // ---- (B1) film pressure of row r(k-1) (needs h rows r(k-2) .. r(k))
         if (pcol && k >= 2 && k <= R + 3) {
-            // the stencil reads slots OFF + 2t - 1 .. OFF + 2t + 2 of rings of NC + 4
-            TFLBM_CHECK(OFF + 2 * t - 1 >= 0 && OFF + 2 * t + 2 < NC + 4, C.status);
+            // the window reads slots j2 - 1 .. j2 + 2 of rings of RW
+            TFLBM_CHECK(j2 >= 1 && j2 + 2 < RW, C.status);
             float2 ih;
-            const float2 p = pair_pressure(hsm[s] + OFF + 2 * t, hsm[s1] + OFF + 2 * t, hsm[s2] + OFF + 2 * t, kap,
-                                           disj, C, ih);
-            rsm[s1][3][t] = ih;
-            *reinterpret_cast<float2*>(&psm[s1][OFF + 2 * t]) = p;
+            const Win Hw = load_win(hsm[s], hsm[s1], hsm[s2], j2);
+            const float2 p = pair_pressure(Hw, kap, disj, C, ih);
+            rsi[s1][t] = ih;
+            *reinterpret_cast<float2*>(&psm[s1][j2]) = p;
         }
         // ---- (B2) force, collision and store of row r(k-3)
         if (ocol && k >= 5) {
             const int o = rstart + (k - 3) * dir;  // inside [ybeg, yend), no wrap
-            TFLBM_CHECK(OFF + 2 * t - 1 >= 0 && OFF + 2 * t + 2 < NC + 4 && o >= 0 && o < ny, C.status);
-            const float* pn = (dir > 0 ? psm[s2] : psm[s]) + OFF + 2 * t;  // row o+1
-            const float* pc = psm[s3] + OFF + 2 * t;
-            const float* ps = (dir > 0 ? psm[s] : psm[s2]) + OFF + 2 * t;  // row o-1
-            const float2 dh = *reinterpret_cast<const float2*>(&hsm[s3][OFF + 2 * t]);
+            TFLBM_CHECK(j2 >= 1 && j2 + 2 < RW && o >= 0 && o < ny, C.status);
+            // rows o+1 and o-1 of the p ring
+            const int sn = dir > 0 ? s2 : s, ss = dir > 0 ? s : s2;
+            const Win Pw = load_win(psm[sn], psm[s3], psm[ss], j2);
+            const float2 dh = lds2(&hsm[s3][j2]);
+            const float4 jj = rsj[s3][t];
             const float2* fp = nullptr;
             if constexpr (!OMEGA1) fp = &fsm[s3][0][t];
-            pair_collide_store<SM, OMEGA1>(pn, pc, ps, dh, rsm[s3][3][t], rsm[s3][0][t], rsm[s3][1][t], rsm[s3][2][t], fp, BX, fout0,
-                                           foutm, o * pitch + c, plane, C);
+            pair_collide_store<SM, OMEGA1>(Pw, dh, rsi[s3][t], make_float2(jj.x, jj.y), make_float2(jj.z, jj.w),
+                                           rse[s3][t], fp, BX, fout0, foutm, o * pitch + c, plane, C);
         }
         wm1 = w0;
         w0 = w1;
