@@ -121,16 +121,23 @@ typedef struct tf_lbm_handle tf_lbm_handle;
 
 /* Kernel launch shape of the fused step (for autotuning).
  *   block_x: CTA width in lattice columns (64, 128 or 256);
- *   rows:    lattice rows marched by one CTA (>= 1);
+ *   rows:    lattice rows marched by one CTA (>= 1): the ny rows are cut
+ *            into ceil(ny / rows) near-equal bands.  The shape chosen by
+ *            tf_lbm_init (and bands-exact candidates of tf_lbm_tune) instead
+ *            uses the number of bands that fills the GPU's resident CTA
+ *            slots once, so its bands need not all have `rows` rows; rows
+ *            then reports the tallest band, and passing it back to
+ *            tf_lbm_set_launch gives ceil(ny / rows) bands;
  *   graph_chunk: steps per captured CUDA graph in tf_lbm_step (0 = none,
  *            otherwise an even number >= 2);
  *   pipeline: 3 = every thread owns two adjacent columns, loads aligned
  *            pairs one (FP32) or two (16-bit) rows ahead, takes the values
  *            that cross a pair boundary from the neighbouring lane and
  *            computes both nodes with paired FP32 instructions (nx even, not
- *            TF_LBM_F64; default for TF_LBM_F16 and TF_LBM_BF16 when nx is
- *            even); 1 = every thread loads its own column into registers,
- *            one row ahead (default otherwise); 2 = every
+ *            TF_LBM_F64; default when nx is even for TF_LBM_F16 and
+ *            TF_LBM_BF16, block_x 64, and for TF_LBM_F32 at tau = 1,
+ *            block_x 128); 1 = every thread loads its own column into
+ *            registers, one row ahead (default otherwise); 2 = every
  *            thread copies its own populations into shared memory by
  *            asynchronous copies, two rows ahead (TF_LBM_F32 and TF_LBM_F64
  *            only); 0 = row segments streamed into shared memory by bulk
@@ -243,8 +250,9 @@ void tf_lbm_tape_destroy(tf_lbm_tape* tape);
  * and keep the fastest.  Each candidate runs 2 untimed and `trial_steps`
  * timed steps (rounded up to even; <= 0 means 16), timed with CUDA events on
  * `stream`.  Candidates: block_x in {64, 128, 256}, every pipeline that
- * applies, and band heights of one, two and three waves of resident CTAs and
- * of 2 to 256 rows.  The state is copied aside first (one population
+ * applies, and band counts of one, two and three waves of resident CTAs
+ * (both balanced bands filling the waves exactly and their rounded-up band
+ * heights) and band heights of 2 to 256 rows.  The state is copied aside first (one population
  * buffer of device memory, freed before return) and put back after, so f
  * and tf_lbm_time are as before the call.  The graph chunk is kept.
  * Synchronises `stream`.  best (host, may be NULL) receives the shape now in

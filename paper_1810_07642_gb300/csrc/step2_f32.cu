@@ -5,9 +5,9 @@
 namespace tflbm {
 
 cudaError_t pair_step_f32(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
-                         const Consts<float>& C, int rows, cudaStream_t st)
+                         const Consts<float>& C, int bands, cudaStream_t st)
 {
-    return pair_step<float>(block_x, fin, fout, kappa, G, C, rows, st);
+    return pair_step<float>(block_x, fin, fout, kappa, G, C, bands, st);
 }
 
 int pair_blocks_per_sm_f32(int block_x, bool omega1, bool kfield)

@@ -14,9 +14,9 @@ static cudaError_t launch_n(const void* fin, void* fout, const void* kappa, cons
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
     const float* k = (const float*)kappa;
     switch (S.block_x) {
-        case 64: return launch_step_bx<SM, float, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 128: return launch_step_bx<SM, float, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 256: return launch_step_bx<SM, float, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 64: return launch_step_bx<SM, float, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
+        case 128: return launch_step_bx<SM, float, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
+        case 256: return launch_step_bx<SM, float, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
         default: return cudaErrorInvalidValue;
     }
 }

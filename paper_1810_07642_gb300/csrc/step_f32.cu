@@ -20,9 +20,9 @@ static cudaError_t launch_typed(const void* fin, void* fout, const void* kappa, 
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(T));
     const T* k = (const T*)kappa;
     switch (S.block_x) {
-        case 64: return launch_step_bx<SM, T, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 128: return launch_step_bx<SM, T, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
-        case 256: return launch_step_bx<SM, T, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, S.rows, st);
+        case 64: return launch_step_bx<SM, T, 64>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
+        case 128: return launch_step_bx<SM, T, 128>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
+        case 256: return launch_step_bx<SM, T, 256>(S.pipeline, f0, fm, g0, gm, k, G, C, launch_bands(S, G.ny), st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -33,9 +33,9 @@ cudaError_t launch_step(int store, const void* fin, void* fout, const void* kapp
 {
     if (S.pipeline == kPipePair) {
         switch (store) {
-            case kStoreF32: return pair_step_f32(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
-            case kStoreF16: return pair_step_f16(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
-            case kStoreBF16: return pair_step_bf16(S.block_x, fin, fout, kappa, G, *C32, S.rows, st);
+            case kStoreF32: return pair_step_f32(S.block_x, fin, fout, kappa, G, *C32, launch_bands(S, G.ny), st);
+            case kStoreF16: return pair_step_f16(S.block_x, fin, fout, kappa, G, *C32, launch_bands(S, G.ny), st);
+            case kStoreBF16: return pair_step_bf16(S.block_x, fin, fout, kappa, G, *C32, launch_bands(S, G.ny), st);
             default: return cudaErrorInvalidValue;
         }
     }

@@ -135,12 +135,14 @@ Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
     s.pipeline = pair ? kPipePair : kPipeLdg;
     int occ = step_blocks_per_sm(store_of(p.dtype), s.pipeline, s.block_x, om1, kfield);
     if (occ < 1) occ = 4;
+    // bands of balanced height (the kernels spread ny rows over them), as
+    // many as fill the resident slots once, but none shorter than 16 rows
     int bands = occ * sms / strips;
+    if (bands > G.ny / 16) bands = G.ny / 16;
     if (bands < 1) bands = 1;
-    int rows = (G.ny + bands - 1) / bands;
-    if (rows < 16) rows = 16;
-    if (rows > 4096) rows = 4096;
-    s.rows = rows;
+    if (bands > 65535) bands = 65535;
+    s.bands = bands;
+    s.rows = (G.ny + bands - 1) / bands;
     return s;
 }
 
@@ -473,6 +475,7 @@ int tf_lbm_set_launch(tf_lbm_handle* H, const tf_lbm_launch* in)
     H->shape.pipeline = in->pipeline;
     H->shape.block_x = bx;
     H->shape.rows = in->rows;
+    H->shape.bands = 0;
     H->graph_chunk = in->graph_chunk;
     return TF_LBM_OK;
 }

@@ -307,6 +307,15 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
             for (int w = 1; w <= 3; ++w) {
                 const int bands = std::max(1, w * occ * sms / strips);
                 rows.push_back(std::max(16, (H->G.ny + bands - 1) / bands));
+                // balanced bands filling w waves exactly (rows need not divide ny)
+                if (bands <= std::min(65535, H->G.ny / 16)) {
+                    Shape s;
+                    s.block_x = bx;
+                    s.pipeline = pipe;
+                    s.bands = bands;
+                    s.rows = (H->G.ny + bands - 1) / bands;
+                    cands.push_back(s);
+                }
             }
             for (int r : {2, 4, 8, 16, 32, 64, 128, 256}) rows.push_back(r);
             for (int r : rows) {
@@ -316,7 +325,7 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
                 s.rows = r;
                 s.pipeline = pipe;
                 bool dup = false;
-                for (auto& c : cands) dup |= c.block_x == bx && c.rows == r && c.pipeline == pipe;
+                for (auto& c : cands) dup |= c.block_x == bx && c.rows == r && c.pipeline == pipe && c.bands == 0;
                 if (!dup) cands.push_back(s);
             }
         }
@@ -361,7 +370,8 @@ int tf_lbm_tune(tf_lbm_handle* H, int32_t trial_steps, tf_lbm_launch* best, void
         return finish(rc);
     }
     H->shape = cands[k];
-    if (H->shape.block_x != old.block_x || H->shape.rows != old.rows || H->shape.pipeline != old.pipeline)
+    if (H->shape.block_x != old.block_x || H->shape.rows != old.rows || H->shape.pipeline != old.pipeline ||
+        H->shape.bands != old.bands)
         handle_drop_graphs(H);
     if (best) {
         best->block_x = H->shape.block_x;

@@ -82,10 +82,21 @@ struct Consts {
 
 // Launch shape of the fused step.
 struct Shape {
-    int block_x;   // 64, 128, 256
-    int rows;      // rows per CTA (band height)
-    int pipeline;  // kPipeTma, kPipeLdg or kPipeAsync
+    int block_x;    // 64, 128, 256
+    int rows;       // rows per CTA (band height)
+    int pipeline;   // kPipeTma, kPipeLdg, kPipeAsync or kPipePair
+    int bands = 0;  // balanced bands per launch; 0: ny / rows rounded up
 };
+
+// Bands of one launch of a step kernel for a shape (at most 65535, the grid's
+// y limit; the kernels balance rows over the bands they are given).
+inline int launch_bands(const Shape& S, int ny)
+{
+    long long b = S.bands > 0 ? S.bands : ((long long)ny + S.rows - 1) / S.rows;
+    if (b > 65535) b = 65535;
+    if (b < 1) b = 1;
+    return (int)b;
+}
 
 // Storage of the 8 moving populations.
 enum Store { kStoreF32 = 0, kStoreF64 = 1, kStoreF16 = 2, kStoreBF16 = 3 };
@@ -102,11 +113,11 @@ int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool k
 // The two-column step (pipeline kPipePair) per storage type (step2_*.cu),
 // and its resident CTAs per SM.
 cudaError_t pair_step_f32(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
-                          const Consts<float>& C, int rows, cudaStream_t st);
+                          const Consts<float>& C, int bands, cudaStream_t st);
 cudaError_t pair_step_f16(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
-                          const Consts<float>& C, int rows, cudaStream_t st);
+                          const Consts<float>& C, int bands, cudaStream_t st);
 cudaError_t pair_step_bf16(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
-                           const Consts<float>& C, int rows, cudaStream_t st);
+                           const Consts<float>& C, int bands, cudaStream_t st);
 int pair_blocks_per_sm_f32(int block_x, bool omega1, bool kfield);
 int pair_blocks_per_sm_f16(int block_x, bool omega1, bool kfield);
 int pair_blocks_per_sm_bf16(int block_x, bool omega1, bool kfield);

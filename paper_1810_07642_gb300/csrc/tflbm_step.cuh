@@ -943,10 +943,8 @@ cudaError_t launch_one(int pipeline, dim3 grid, const T* fin0, const SM* finm, T
 
 template <typename SM, typename T, int BX>
 cudaError_t launch_step_bx(int pipeline, const T* fin0, const SM* finm, T* fout0, SM* foutm,
-                           const T* kappa, const Geom& G, const Consts<T>& C, int rows, cudaStream_t st)
+                           const T* kappa, const Geom& G, const Consts<T>& C, int bands, cudaStream_t st)
 {
-    int bands = (G.ny + rows - 1) / rows;
-    if (bands > 65535) bands = 65535;
     dim3 grid((G.nx + BX - 5) / (BX - 4), bands);
     const bool om1 = (C.omega == T(1));
     if (kappa) {

@@ -552,10 +552,8 @@ k_step2(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __re
 
 template <typename SM, int BX>
 cudaError_t launch_pair_bx(const float* fin0, const SM* finm, float* fout0, SM* foutm, const float* kappa,
-                           const Geom& G, const Consts<float>& C, int rows, cudaStream_t st)
+                           const Geom& G, const Consts<float>& C, int bands, cudaStream_t st)
 {
-    int bands = (G.ny + rows - 1) / rows;
-    if (bands > 65535) bands = 65535;
     constexpr int W = 2 * BX - 4;
     const dim3 grid((G.nx + W - 1) / W, bands);
     const bool om1 = C.omega == 1.0f;
@@ -578,7 +576,7 @@ int bps_pair_one()
 // The paired step for one storage type.
 template <typename SM>
 cudaError_t pair_step(int block_x, const void* fin, void* fout, const void* kappa, const Geom& G,
-                      const Consts<float>& C, int rows, cudaStream_t st)
+                      const Consts<float>& C, int bands, cudaStream_t st)
 {
     const float* f0 = (const float*)fin;
     const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(float));
@@ -586,9 +584,9 @@ cudaError_t pair_step(int block_x, const void* fin, void* fout, const void* kapp
     SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
     const float* k = (const float*)kappa;
     switch (block_x) {
-        case 64: return launch_pair_bx<SM, 32>(f0, fm, g0, gm, k, G, C, rows, st);
-        case 128: return launch_pair_bx<SM, 64>(f0, fm, g0, gm, k, G, C, rows, st);
-        case 256: return launch_pair_bx<SM, 128>(f0, fm, g0, gm, k, G, C, rows, st);
+        case 64: return launch_pair_bx<SM, 32>(f0, fm, g0, gm, k, G, C, bands, st);
+        case 128: return launch_pair_bx<SM, 64>(f0, fm, g0, gm, k, G, C, bands, st);
+        case 256: return launch_pair_bx<SM, 128>(f0, fm, g0, gm, k, G, C, bands, st);
         default: return cudaErrorInvalidValue;
     }
 }
