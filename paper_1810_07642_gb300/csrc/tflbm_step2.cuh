@@ -423,12 +423,21 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 eb = IO::dec1(qe[rb][1]);  // l = 2 or 4
                 ed = IO::dec1(qe[rb][2]);  // l = 8 or 6
             }
-            // the loads of row r(k+PF) go out before this row's arithmetic
-            if constexpr (PF == 2) {
-                if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
-            } else {
-                if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
-            }
+            // the loads of row r(k+PF) go out before this row's arithmetic.
+            // FP32 values are used as loaded, in the registers the next loads
+            // land in: at tau = 1 the partial sums are formed first, so the
+            // loads go out without waiting for (or copying) this row (one
+            // box: 56.0 -> 52.7 us per 2048^2 step, long-scoreboard stalls
+            // 5.3 -> 3.8 per issue)
+            auto issue_next = [&]() {
+                if constexpr (PF == 2) {
+                    if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
+                } else {
+                    if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
+                }
+            };
+            constexpr bool EARLY = NARROW || !OMEGA1;
+            if constexpr (EARLY) issue_next();
             if (KFIELD && pcol)
                 kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)w0 * nx + c) >> 1, npair,
                                                                           C.status)];
@@ -439,13 +448,17 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
             if constexpr (OMEGA1) {
                 const float2 Pc = padd(padd(v[0], v[1]), v[7]), Py = psub(v[1], v[7]);
                 const float2 Qc = padd(padd(v[4], v[3]), v[5]), Qy = psub(v[3], v[5]);
+                const float2 s26 = padd(v[2], v[6]), d26 = psub(v[2], v[6]);
+                const float es = (ea + eb) + ed, ey = eb - ed;
+                if constexpr (!EARLY) issue_next();
                 float pl = __shfl_up_sync(0xffffffffu, Pc.y, 1), pyl = __shfl_up_sync(0xffffffffu, Py.y, 1);
                 float qr = __shfl_down_sync(0xffffffffu, Qc.x, 1), qyr = __shfl_down_sync(0xffffffffu, Qy.x, 1);
-                if (lane == 0) { pl = (ea + eb) + ed; pyl = eb - ed; }
-                if (lane == 31) { qr = (ea + eb) + ed; qyr = eb - ed; }
+                if (lane == 0) { pl = es; pyl = ey; }
+                if (lane == 31) { qr = es; qyr = ey; }
                 Rs = make_float2(pl, Pc.x);
                 Ls = make_float2(Qc.y, qr);
-                jyr = padd(psub(v[2], v[6]), padd(make_float2(pyl, Py.x), make_float2(Qy.y, qyr)));
+                jyr = padd(d26, padd(make_float2(pyl, Py.x), make_float2(Qy.y, qyr)));
+                tot = padd(s26, padd(Rs, Ls));
             } else {
                 // the single arriving values, kept for the relaxation
                 float u1 = __shfl_up_sync(0xffffffffu, v[0].y, 1);
@@ -468,10 +481,10 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 Rs = padd(padd(n[0], n[1]), n[7]);
                 Ls = padd(padd(n[4], n[3]), n[5]);
                 jyr = padd(padd(psub(n[2], n[6]), psub(n[1], n[7])), psub(n[3], n[5]));
+                tot = padd(padd(n[2], n[6]), padd(Rs, Ls));
 #pragma unroll
                 for (int l = 0; l < 8; ++l) fsm[s][l][t] = n[l];
             }
-            tot = padd(padd(v[2], v[6]), padd(Rs, Ls));
             // h - href: the moving total is small, the last addition is
             // error-free (see sum9)
             float2 dh, er, jx, jy;
