@@ -382,6 +382,10 @@ def batched_sweep(steps: int = 30000, timed: int = 400):
             B.set_launch(queue=queue, graph_chunk=chunk)
             forms[f"queue{queue}_graph{chunk}"] = mlups(B.step, nodes, timed)
     out["mlups_forms_at_tuned_shape"] = forms
+    # the one-column kernel in the shape its own tuning chose for this sweep
+    # (64-column CTAs, 60-row bands, one CTA per item, no graph)
+    B.set_launch(block_x=64, rows=60, queue=0, graph_chunk=0, pipeline=1)
+    out["mlups_batched_one_column"] = mlups(B.step, nodes, timed)
     B.set_launch(**out["tuned_launch"])
     B.close()
     for f in films:
@@ -778,8 +782,9 @@ def run_sweep(args):
         B = FilmBatch(films, stream=stream)
     nodes = sum(f.nx * f.ny for f in films)
     if args.batch_launch:
-        bx, rows, chunk, queue = (int(v) for v in args.batch_launch.split(","))
-        B.set_launch(block_x=bx, rows=rows, graph_chunk=chunk, queue=queue)
+        v = [int(x) for x in args.batch_launch.split(",")]
+        B.set_launch(block_x=v[0], rows=v[1], graph_chunk=v[2], queue=v[3],
+                     pipeline=v[4] if len(v) > 4 else None)
         launch = B.launch
     else:
         launch = B.tune(16)
@@ -918,7 +923,7 @@ def main():
                     help="patterned workload: block_x,rows,pipeline of the fused step instead of "
                          "the library's default shape")
     ap.add_argument("--batch-launch", default="",
-                    help="sweep workload: block_x,rows,graph_chunk,queue instead of autotuning")
+                    help="sweep workload: block_x,rows,graph_chunk,queue[,pipeline] instead of autotuning")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the 16-bit storage, adjoint and batched-sweep measurements")
     args = ap.parse_args()

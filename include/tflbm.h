@@ -324,12 +324,19 @@ typedef struct tf_lbm_batch tf_lbm_batch;
  *   graph_chunk: steps per captured CUDA graph (0 or even, <= 4096);
  *   queue:   0 = one CTA per work item; 1 = a persistent grid of one wave of
  *            resident CTAs, each taking items from an atomic counter until
- *            none are left. */
+ *            none are left;
+ *   pipeline: 1 = one column per thread; 3 = two columns per thread, as in
+ *            tf_lbm_launch (every domain's nx even, not TF_LBM_F64).  The
+ *            default is 3 where it applies, for TF_LBM_F16 and TF_LBM_BF16
+ *            always and for TF_LBM_F32 when every tau is 1 (as for a single
+ *            handle), else 1.  Both run the node arithmetic of the
+ *            single-handle kernel of the same pipeline. */
 typedef struct tf_lbm_batch_launch {
     int32_t block_x;
     int32_t rows;
     int32_t graph_chunk;
     int32_t queue;
+    int32_t pipeline;
 } tf_lbm_batch_launch;
 
 /* Create a batch of `count` >= 1 handles (host array, copied).  ARG error
@@ -342,8 +349,8 @@ int tf_lbm_batch_step(tf_lbm_batch* B, int64_t nsteps, void* stream);
  * (cudaDeviceSynchronize); ARG error on an invalid shape. */
 int tf_lbm_batch_get_launch(const tf_lbm_batch* B, tf_lbm_batch_launch* out);
 int tf_lbm_batch_set_launch(tf_lbm_batch* B, const tf_lbm_batch_launch* in);
-/* As tf_lbm_tune, over block_x, rows and queue, for the whole batch (every
- * handle's state copied aside and put back). */
+/* As tf_lbm_tune, over block_x, rows, queue and the pipelines that apply,
+ * for the whole batch (every handle's state copied aside and put back). */
 int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch* best, void* stream);
 /* tf_lbm_diagnostics of every handle in two launches: out is a device array
  * of `count` tf_lbm_diag, in the order of the handles. */

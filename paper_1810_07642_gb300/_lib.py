@@ -60,7 +60,8 @@ class Launch(ctypes.Structure):
 class BatchLaunch(ctypes.Structure):
     """Mirror of tf_lbm_batch_launch."""
     _fields_ = [("block_x", ctypes.c_int32), ("rows", ctypes.c_int32),
-                ("graph_chunk", ctypes.c_int32), ("queue", ctypes.c_int32)]
+                ("graph_chunk", ctypes.c_int32), ("queue", ctypes.c_int32),
+                ("pipeline", ctypes.c_int32)]
 
 
 _lib = None
@@ -284,8 +285,9 @@ def tf_lbm_batch_get_launch(batch: int) -> BatchLaunch:
     return out
 
 
-def tf_lbm_batch_set_launch(batch: int, block_x: int, rows: int, graph_chunk: int, queue: int = 0) -> None:
-    L = BatchLaunch(block_x, rows, graph_chunk, queue)
+def tf_lbm_batch_set_launch(batch: int, block_x: int, rows: int, graph_chunk: int, queue: int = 0,
+                            pipeline: int = 1) -> None:
+    L = BatchLaunch(block_x, rows, graph_chunk, queue, pipeline)
     _bcheck(lib().tf_lbm_batch_set_launch(_VP(batch), ctypes.byref(L)), _VP(batch))
 
 

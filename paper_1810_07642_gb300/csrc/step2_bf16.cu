@@ -15,4 +15,9 @@ int pair_blocks_per_sm_bf16(int block_x, bool omega1, bool kfield)
     return pair_blocks_per_sm<__nv_bfloat16>(block_x, omega1, kfield);
 }
 
+cudaError_t pair_step_batch_bf16(const BatchLaunch& L, cudaStream_t st)
+{
+    return pair_step_batch<__nv_bfloat16>(L, st);
+}
+
 }  // namespace tflbm

@@ -15,4 +15,9 @@ int pair_blocks_per_sm_f16(int block_x, bool omega1, bool kfield)
     return pair_blocks_per_sm<__half>(block_x, omega1, kfield);
 }
 
+cudaError_t pair_step_batch_f16(const BatchLaunch& L, cudaStream_t st)
+{
+    return pair_step_batch<__half>(L, st);
+}
+
 }  // namespace tflbm

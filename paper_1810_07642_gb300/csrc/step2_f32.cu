@@ -15,4 +15,9 @@ int pair_blocks_per_sm_f32(int block_x, bool omega1, bool kfield)
     return pair_blocks_per_sm<float>(block_x, omega1, kfield);
 }
 
+cudaError_t pair_step_batch_f32(const BatchLaunch& L, cudaStream_t st)
+{
+    return pair_step_batch<float>(L, st);
+}
+
 }  // namespace tflbm

@@ -73,6 +73,14 @@ int step_blocks_per_sm(int store, int pipeline, int block_x, bool omega1, bool k
 
 cudaError_t launch_step_batch(int store, const BatchLaunch& L, cudaStream_t st)
 {
+    if (L.pair) {
+        switch (store) {
+            case kStoreF32: return pair_step_batch_f32(L, st);
+            case kStoreF16: return pair_step_batch_f16(L, st);
+            case kStoreBF16: return pair_step_batch_bf16(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (store) {
         case kStoreF32: return launch_batch_typed<float, float>(L, st);
         case kStoreF64: return launch_batch_typed<double, double>(L, st);

@@ -2,8 +2,10 @@
 // the launch-shape autotuner and the on-device film diagnostics
 // (include/tflbm.h).
 //
-// A batched step is one launch of k_step_batch over a flat table of work
-// items (domain, column strip, row band); a table of per-domain records
+// A batched step is one launch of k_step_batch (one column per thread) or
+// k_step2_batch (two columns per thread, every nx even, FP32 compute type)
+// over a flat table of work items (domain, column strip, row band); a table
+// of per-domain records
 // (geometry, constants, the two population buffers, kappa) lives in device
 // memory next to it.  The records name the buffers in the order they had
 // when the table was written; a phase bit counts the steps since then, so a
@@ -33,6 +35,7 @@ struct tf_lbm_batch {
     bool dbl = false;
     bool om1 = false;  // every domain has omega == 1 in the compute type
     bool kf = false;   // some domain has a kappa field: every domain gets one
+    bool pair_ok = false;  // the two-column kernel applies (FP32 compute type, every nx even)
     std::vector<void*> kfill;  // filled kappa fields of the uniform domains (kf only)
     std::vector<int> cur0;     // each handle's buffer index when the table was written
     int phase = 0;             // steps taken since then, mod 2
@@ -42,7 +45,7 @@ struct tf_lbm_batch {
     int nitems = 0;
     int* queue = nullptr;  // item counter and finished-CTA counter (zero between launches)
     int grid = 0;
-    tf_lbm_batch_launch L{64, 64, 0, 0};
+    tf_lbm_batch_launch L{64, 64, 0, 0, kPipeLdg};
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     double* dpart = nullptr;  // diagnostics partials
@@ -128,11 +131,12 @@ int rows_for_slots(const tf_lbm_batch* B, int bx, long long slots)
     return hi;
 }
 
-int batch_occupancy(const tf_lbm_batch* B, int bx)
+int batch_occupancy(const tf_lbm_batch* B, int bx, int pipeline)
 {
     int occ = 0;
     BatchLaunch q{};
     q.block_x = bx;
+    q.pair = pipeline == kPipePair;
     q.omega1 = B->om1;
     q.kfield = B->kf;
     q.query_occupancy = &occ;
@@ -196,7 +200,7 @@ int write_items(tf_lbm_batch* B, const tf_lbm_batch_launch& L, cudaStream_t st)
     B->nitems = (int)n;
     int grid = (int)n;
     if (L.queue) {
-        const int occ = batch_occupancy(B, L.block_x);
+        const int occ = batch_occupancy(B, L.block_x, L.pipeline);
         const long long slots = (long long)std::max(occ, 1) * sm_count();
         grid = (int)std::min<long long>(n, slots);
     }
@@ -208,6 +212,7 @@ cudaError_t launch_batch(tf_lbm_batch* B, int parity, cudaStream_t st)
 {
     BatchLaunch q{};
     q.block_x = B->L.block_x;
+    q.pair = B->L.pipeline == kPipePair;
     q.omega1 = B->om1;
     q.kfield = B->kf;
     q.items = B->items;
@@ -228,6 +233,10 @@ int validate_batch_launch(tf_lbm_batch* B, const tf_lbm_batch_launch* in)
     if (in->graph_chunk < 0 || (in->graph_chunk % 2) != 0 || in->graph_chunk > 4096)
         return bfail(B, TF_LBM_ERR_ARG, "graph_chunk must be 0 or an even number <= 4096");
     if (in->queue != 0 && in->queue != 1) return bfail(B, TF_LBM_ERR_ARG, "queue must be 0 or 1");
+    if (in->pipeline != kPipeLdg && in->pipeline != kPipePair)
+        return bfail(B, TF_LBM_ERR_ARG, "pipeline must be 1 (one column per thread) or 3 (two columns per thread)");
+    if (in->pipeline == kPipePair && !B->pair_ok)
+        return bfail(B, TF_LBM_ERR_ARG, "the two-column pipeline needs every nx even and an FP32 compute type");
     return TF_LBM_OK;
 }
 
@@ -486,9 +495,11 @@ int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32
     B->cur0.assign(count, 0);
     B->kfill.assign(count, nullptr);
     B->om1 = true;
+    B->pair_ok = !B->dbl;
     for (auto* H : B->hs) {
         B->kf |= H->kappa != nullptr;
         B->om1 &= B->dbl ? make_consts<double>(H).omega == 1.0 : make_consts<float>(H).omega == 1.0f;
+        B->pair_ok &= pair_pipeline_ok(H->G.nx, B->store);
     }
     auto bail = [&](int code) {
         set_thread_error(B->err);
@@ -517,8 +528,11 @@ int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32
     int rc = write_table(B, st);
     if (rc) return bail(rc);
 
-    // default shape: 64-wide CTAs unless most domains are wide, band height
-    // filling one wave of resident CTAs
+    // default shape: the two-column kernel where it applies and a single
+    // handle would take it (16-bit storage, or FP32 with every tau == 1), 64
+    // columns per CTA for 16-bit storage and 128 for FP32; else the
+    // one-column kernel, 64-wide CTAs unless most domains are wide; band
+    // height filling one wave of resident CTAs
     std::vector<int> widths;
     long long nodes = 0;
     for (auto* H : B->hs) {
@@ -527,8 +541,11 @@ int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32
     }
     std::nth_element(widths.begin(), widths.begin() + widths.size() / 2, widths.end());
     tf_lbm_batch_launch L{};
-    L.block_x = widths[widths.size() / 2] >= 1024 ? 128 : 64;
-    const int occ = std::max(1, batch_occupancy(B, L.block_x));
+    const bool narrow = B->store == kStoreF16 || B->store == kStoreBF16;
+    L.pipeline = B->pair_ok && (narrow || B->om1) ? kPipePair : kPipeLdg;
+    if (L.pipeline == kPipePair) L.block_x = narrow ? 64 : 128;
+    else L.block_x = widths[widths.size() / 2] >= 1024 ? 128 : 64;
+    const int occ = std::max(1, batch_occupancy(B, L.block_x, L.pipeline));
     L.rows = rows_for_slots(B, L.block_x, (long long)occ * sm_count());
     L.graph_chunk = nodes <= (1LL << 20) ? 64 : 0;
     L.queue = 0;
@@ -614,17 +631,20 @@ int tf_lbm_batch_tune(tf_lbm_batch* B, int32_t trial_steps, tf_lbm_batch_launch*
     for (auto* H : B->hs) ymax = std::max(ymax, H->G.ny);
 
     std::vector<tf_lbm_batch_launch> cands;
-    for (int bx : {64, 128, 256}) {
-        const int occ = std::max(1, batch_occupancy(B, bx));
-        std::vector<int> rows;
-        for (int w = 1; w <= 3; ++w) rows.push_back(rows_for_slots(B, bx, (long long)w * occ * sms));
-        for (int r : {8, 16, 32, 64, 128, 256}) rows.push_back(std::min(r, ymax));
-        for (int r : rows)
-            for (int q : {0, 1}) {
-                bool dup = false;
-                for (auto& c : cands) dup |= c.block_x == bx && c.rows == r && c.queue == q;
-                if (!dup) cands.push_back(tf_lbm_batch_launch{bx, r, B->L.graph_chunk, q});
-            }
+    for (int pipe : {kPipePair, kPipeLdg}) {
+        if (pipe == kPipePair && !B->pair_ok) continue;
+        for (int bx : {64, 128, 256}) {
+            const int occ = std::max(1, batch_occupancy(B, bx, pipe));
+            std::vector<int> rows;
+            for (int w = 1; w <= 3; ++w) rows.push_back(rows_for_slots(B, bx, (long long)w * occ * sms));
+            for (int r : {8, 16, 32, 64, 128, 256}) rows.push_back(std::min(r, ymax));
+            for (int r : rows)
+                for (int q : {0, 1}) {
+                    bool dup = false;
+                    for (auto& c : cands) dup |= c.block_x == bx && c.rows == r && c.queue == q && c.pipeline == pipe;
+                    if (!dup) cands.push_back(tf_lbm_batch_launch{bx, r, B->L.graph_chunk, q, pipe});
+                }
+        }
     }
 
     // copy every state aside

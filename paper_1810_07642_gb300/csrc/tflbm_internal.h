@@ -141,6 +141,7 @@ struct BatchDomain {
 // SM of the selected kernel are written there instead.
 struct BatchLaunch {
     int block_x;
+    bool pair;  // the two-column kernel (nx even in every domain, FP32 compute type)
     bool omega1, kfield;
     const BatchItem* items;
     int nitems;
@@ -151,6 +152,10 @@ struct BatchLaunch {
     int* query_occupancy;
 };
 cudaError_t launch_step_batch(int store, const BatchLaunch& L, cudaStream_t st);
+// The batched two-column step per storage type (step2_*.cu).
+cudaError_t pair_step_batch_f32(const BatchLaunch& L, cudaStream_t st);
+cudaError_t pair_step_batch_f16(const BatchLaunch& L, cudaStream_t st);
+cudaError_t pair_step_batch_bf16(const BatchLaunch& L, cudaStream_t st);
 
 // Storage convention: plane 0 holds f_0 - href, planes 1..8 hold f_l (or its
 // 16-bit encoding, see Consts).  In

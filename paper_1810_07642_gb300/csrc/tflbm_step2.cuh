@@ -423,12 +423,12 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                 eb = IO::dec1(qe[rb][1]);  // l = 2 or 4
                 ed = IO::dec1(qe[rb][2]);  // l = 8 or 6
             }
-            // the loads of row r(k+PF) go out before this row's arithmetic.
-            // FP32 values are used as loaded, in the registers the next loads
-            // land in: at tau = 1 the partial sums are formed first, so the
-            // loads go out without waiting for (or copying) this row (one
-            // box: 56.0 -> 52.7 us per 2048^2 step, long-scoreboard stalls
-            // 5.3 -> 3.8 per issue)
+            // the loads of row r(k+PF) go out before this row's arithmetic;
+            // at tau = 1 right after the partial sums, which free the
+            // registers they land in (FP32 values are used as loaded), so the
+            // loads neither wait for nor copy this row (one box, 2048^2 step:
+            // FP32 56.0 -> 52.7 us, long-scoreboard stalls 5.3 -> 3.8 per
+            // issue; FP16 46.5 -> 45.3 us, BF16 47.1 -> 45.4 us)
             auto issue_next = [&]() {
                 if constexpr (PF == 2) {
                     if (k + 2 <= R + 3) load_row(std::integral_constant<int, rb>{}, w1, w2, w3);
@@ -436,7 +436,7 @@ __device__ __forceinline__ void step_band2(const float* __restrict__ fin0, const
                     if (k + 1 <= R + 3) load_row(std::integral_constant<int, rb>{}, w0, w1, w2);
                 }
             };
-            constexpr bool EARLY = NARROW || !OMEGA1;
+            constexpr bool EARLY = !OMEGA1;
             if constexpr (EARLY) issue_next();
             if (KFIELD && pcol)
                 kap_n = reinterpret_cast<const float2*>(kappa)[TFLBM_IDX(((long long)w0 * nx + c) >> 1, npair,
@@ -557,6 +557,89 @@ k_step2(const float* __restrict__ fin0, const SM* __restrict__ finm, float* __re
 {
     dependent_launch_entry();
     step_band2<SM, BX, OMEGA1, KFIELD>(fin0, finm, fout0, foutm, kappa, G, C, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: the work items of k_step_batch (a band of a strip of one
+// domain; block_x columns per strip in both kernels), each run as
+// step_band2 with its domain's geometry and constants.  Every domain reads
+// its buffer `parity` and writes the other one; queue as in k_step_batch (a
+// persistent grid taking items from a counter, reset by the last CTA; no CTA
+// waits on another).  Needs every domain's nx even and the FP32 compute type.
+template <typename SM, int BX, bool OMEGA1, bool KFIELD>
+__device__ __forceinline__ void batch_item2(const BatchItem it, const BatchDomain<float>* __restrict__ doms,
+                                            int parity)
+{
+    const BatchDomain<float>& D = doms[it.dom];
+    const Geom G = D.G;
+    Consts<float> C = D.C;
+    C.flip = parity;
+    const void* fin = D.buf[parity];
+    void* fout = D.buf[parity ^ 1];
+    const float* f0 = (const float*)fin;
+    const SM* fm = (const SM*)((const char*)fin + G.plane * sizeof(float));
+    float* g0 = (float*)fout;
+    SM* gm = (SM*)((char*)fout + G.plane * sizeof(float));
+    step_band2<SM, BX, OMEGA1, KFIELD>(f0, fm, g0, gm, D.kappa, G, C, it.strip, it.band, it.nbands);
+}
+
+template <typename SM, int BX, bool OMEGA1, bool KFIELD>
+__global__ void __launch_bounds__(BX, 768 / BX)
+k_step2_batch(const BatchItem* __restrict__ items, int nitems, const BatchDomain<float>* __restrict__ doms,
+              int parity, int* queue)
+{
+    dependent_launch_entry();
+    if (!queue) {
+        batch_item2<SM, BX, OMEGA1, KFIELD>(items[blockIdx.x], doms, parity);
+        return;
+    }
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();  // the previous item is done with the shared rings and with `next`
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int i = next;
+        if (i >= nitems) break;
+        batch_item2<SM, BX, OMEGA1, KFIELD>(items[i], doms, parity);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {  // every CTA has taken its last item
+            queue[0] = 0;
+            queue[1] = 0;
+        }
+    }
+}
+
+template <typename SM, int BX, bool OM1, bool KF>
+cudaError_t batch2_one(const BatchLaunch& L, cudaStream_t st)
+{
+    const BatchDomain<float>* d = (const BatchDomain<float>*)L.doms;
+    if (L.query_occupancy) {
+        int n = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2_batch<SM, BX, OM1, KF>, BX, 0);
+        *L.query_occupancy = e == cudaSuccess ? n : 0;
+        return e;
+    }
+    return launch_dependent(k_step2_batch<SM, BX, OM1, KF>, dim3(L.grid), BX, 0, st, L.items, L.nitems, d, L.parity,
+                            L.queue);
+}
+
+// The batched paired step for one storage type (L.block_x columns per CTA).
+template <typename SM>
+cudaError_t pair_step_batch(const BatchLaunch& L, cudaStream_t st)
+{
+    auto pick = [&](auto bx_c) {
+        constexpr int BX = decltype(bx_c)::value;
+        if (L.kfield) return L.omega1 ? batch2_one<SM, BX, true, true>(L, st) : batch2_one<SM, BX, false, true>(L, st);
+        return L.omega1 ? batch2_one<SM, BX, true, false>(L, st) : batch2_one<SM, BX, false, false>(L, st);
+    };
+    switch (L.block_x) {
+        case 64: return pick(std::integral_constant<int, 32>{});
+        case 128: return pick(std::integral_constant<int, 64>{});
+        case 256: return pick(std::integral_constant<int, 128>{});
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------------------

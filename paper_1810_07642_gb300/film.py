@@ -182,17 +182,20 @@ class FilmBatch:
     @property
     def launch(self):
         l = L.tf_lbm_batch_get_launch(self.batch)
-        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue,
+                    pipeline=l.pipeline)
 
-    def set_launch(self, block_x=None, rows=None, graph_chunk=None, queue=None):
+    def set_launch(self, block_x=None, rows=None, graph_chunk=None, queue=None, pipeline=None):
         cur = self.launch
         L.tf_lbm_batch_set_launch(self.batch, block_x or cur["block_x"], rows or cur["rows"],
                                   cur["graph_chunk"] if graph_chunk is None else graph_chunk,
-                                  cur["queue"] if queue is None else queue)
+                                  cur["queue"] if queue is None else queue,
+                                  cur["pipeline"] if pipeline is None else pipeline)
 
     def tune(self, trial_steps: int = 16):
         l = L.tf_lbm_batch_tune(self.batch, trial_steps, self._st)
-        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue)
+        return dict(block_x=l.block_x, rows=l.rows, graph_chunk=l.graph_chunk, queue=l.queue,
+                    pipeline=l.pipeline)
 
     def diagnostics(self, h_wet: float, mode=(1, 0), out=None):
         """(count, 12) float64 device tensor of tf_lbm_diag rows, one per film."""

@@ -50,11 +50,13 @@ def rel_linf(a, b):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / np.abs(b).max())
 
 
-def uneven_specs(tau=(1.0, 1.0, 1.0, 1.0)):
+def uneven_specs(tau=(1.0, 1.0, 1.0, 1.0), even=False):
     """Four uneven domains: patterned theta fields and uniform angles mixed,
-    one narrower than a CTA, one smaller than the stencil."""
+    one narrower than a CTA, one smaller than the stencil (even: every nx
+    even, as the two-column kernel needs)."""
     out = []
-    for i, (nx, ny) in enumerate([(37, 29), (130, 70), (64, 32), (5, 7)]):
+    sizes = [(38, 29), (130, 70), (64, 32), (6, 7)] if even else [(37, 29), (130, 70), (64, 32), (5, 7)]
+    for i, (nx, ny) in enumerate(sizes):
         h0, th, p = inputs.small_random(nx, ny, seed=10 + i, amp=0.1)
         p["tau"] = tau[i]
         p["g"] = 1e-3 * (i - 1)
@@ -75,11 +77,18 @@ def host_h(film):
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "f16", "bf16"])
 @pytest.mark.parametrize("taus", [(1.0, 1.0, 1.0, 1.0), (0.8, 1.0, 1.3, 0.6)])
-def test_batch_parity_with_oracle(dtype, taus):
-    specs = uneven_specs(taus)
+@pytest.mark.parametrize("even", [False, True])
+def test_batch_parity_with_oracle(dtype, taus, even):
+    """Odd widths take the one-column kernel; even widths the two-column one
+    (its default for 16-bit storage and for FP32 at tau = 1, asked for
+    explicitly otherwise)."""
+    specs = uneven_specs(taus, even=even)
     films = make_films(specs, dtype)
     m0 = [f.mass() for f in films]
     with FilmBatch(films) as B:
+        if even and dtype != "f64":
+            B.set_launch(pipeline=3)
+        assert B.launch["pipeline"] == (3 if even and dtype != "f64" else 1)
         B.step(1000)
         torch.cuda.synchronize()
         for (h0, th, p), f, m in zip(specs, films, m0):
@@ -120,19 +129,21 @@ def test_sliding_drop_sweep_parity(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
-def test_batch_matches_single_domain_path(dtype):
-    """A batched step and a single-domain step with the same CTA width and
-    band height agree to rounding.  The two kernels may contract different
-    multiply-adds; with 16-bit storage such a difference can flip the
-    rounding of a stored deviation (2^-11 relative), hence the looser bound."""
-    specs = uneven_specs()
+@pytest.mark.parametrize("pipeline", [1, 3])
+def test_batch_matches_single_domain_path(dtype, pipeline):
+    """A batched step and a single-domain step with the same pipeline, CTA
+    width and band height agree to rounding.  The two kernels may contract
+    different multiply-adds; with 16-bit storage such a difference can flip
+    the rounding of a stored deviation (2^-11 relative), hence the looser
+    bound."""
+    specs = uneven_specs(even=pipeline == 3)
     singles = make_films(specs, dtype)
     batched = make_films(specs, dtype)
     for f in singles:
-        f.set_launch(block_x=64, rows=16, graph_chunk=0, pipeline=1)
+        f.set_launch(block_x=64, rows=16, graph_chunk=0, pipeline=pipeline)
         f.step(200)
     with FilmBatch(batched) as B:
-        B.set_launch(block_x=64, rows=16, graph_chunk=0, queue=0)
+        B.set_launch(block_x=64, rows=16, graph_chunk=0, queue=0, pipeline=pipeline)
         B.step(200)
         for a, b in zip(singles, batched):
             sa = a.get_state().cpu().numpy()
@@ -141,14 +152,15 @@ def test_batch_matches_single_domain_path(dtype):
             assert np.abs(sa - sb).max() <= tol * np.abs(sa).max()
 
 
-def test_batch_launch_shapes_are_bit_identical():
-    specs = uneven_specs((0.9, 0.9, 0.9, 0.9))
+@pytest.mark.parametrize("pipeline", [1, 3])
+def test_batch_launch_shapes_are_bit_identical(pipeline):
+    specs = uneven_specs((0.9, 0.9, 0.9, 0.9), even=pipeline == 3)
     ref = None
     for shape in [dict(block_x=64, rows=16, queue=0), dict(block_x=64, rows=5, queue=1),
                   dict(block_x=64, rows=200, queue=1), dict(block_x=64, rows=1, queue=0)]:
         films = make_films(specs, "f32")
         with FilmBatch(films) as B:
-            B.set_launch(graph_chunk=4, **shape)
+            B.set_launch(graph_chunk=4, pipeline=pipeline, **shape)
             B.step(50)
             states = [f.get_state().cpu().numpy() for f in films]
         if ref is None:
@@ -187,6 +199,7 @@ def test_batch_tuner_keeps_state_and_time():
         before = [f.get_state().cpu().numpy() for f in films]
         best = B.tune(trial_steps=4)
         assert best["block_x"] in (64, 128, 256) and best["rows"] >= 1 and best["queue"] in (0, 1)
+        assert best["pipeline"] == 1  # odd widths: the one-column kernel only
         assert B.launch == best
         after = [f.get_state().cpu().numpy() for f in films]
         for a, b in zip(before, after):
