@@ -398,7 +398,8 @@ void tf_lbm_destroy(tf_lbm_handle* H);
  * call on H. */
 const char* tf_lbm_last_error(const tf_lbm_handle* H);
 
-/* Library version, major * 10000 + minor * 100 + patch. */
+/* Library version, major * 10000 + minor * 100 + patch.  0.2.0 added the
+ * pipeline field to tf_lbm_batch_launch (the struct grew by one int32). */
 int32_t tf_lbm_version(void);
 
 #ifdef __cplusplus

@@ -221,7 +221,7 @@ static_assert(kStatusTimeout == TF_LBM_STATUS_TIMEOUT, "status bits out of sync"
 
 extern "C" {
 
-int32_t tf_lbm_version(void) { return 100; }
+int32_t tf_lbm_version(void) { return 200; }
 
 const char* tf_lbm_last_error(const tf_lbm_handle* H)
 {
