@@ -134,10 +134,10 @@ typedef struct tf_lbm_handle tf_lbm_handle;
  *            pairs one (FP32) or two (16-bit) rows ahead, takes the values
  *            that cross a pair boundary from the neighbouring lane and
  *            computes both nodes with paired FP32 instructions (nx even, not
- *            TF_LBM_F64; default when nx is even for TF_LBM_F16 and
- *            TF_LBM_BF16, block_x 64, and for TF_LBM_F32 at tau = 1,
- *            block_x 128); 1 = every thread loads its own column into
- *            registers, one row ahead (default otherwise); 2 = every
+ *            TF_LBM_F64; default at tau = 1 when nx is even, block_x 64 for
+ *            TF_LBM_F16 and TF_LBM_BF16, 128 for TF_LBM_F32); 1 = every
+ *            thread loads its own column into registers, one row ahead
+ *            (default otherwise); 2 = every
  *            thread copies its own populations into shared memory by
  *            asynchronous copies, two rows ahead (TF_LBM_F32 and TF_LBM_F64
  *            only); 0 = row segments streamed into shared memory by bulk
@@ -327,9 +327,8 @@ typedef struct tf_lbm_batch tf_lbm_batch;
  *            none are left;
  *   pipeline: 1 = one column per thread; 3 = two columns per thread, as in
  *            tf_lbm_launch (every domain's nx even, not TF_LBM_F64).  The
- *            default is 3 where it applies, for TF_LBM_F16 and TF_LBM_BF16
- *            always and for TF_LBM_F32 when every tau is 1 (as for a single
- *            handle), else 1.  Both run the node arithmetic of the
+ *            default is 3 where it applies and every tau is 1 (as for a
+ *            single handle), else 1.  Both run the node arithmetic of the
  *            single-handle kernel of the same pipeline. */
 typedef struct tf_lbm_batch_launch {
     int32_t block_x;

@@ -106,8 +106,8 @@ int store_of(int dtype)
     }
 }
 
-// Default launch shape: the two-column kernel where it applies (CTAs 64
-// columns wide for 16-bit storage, 128 for FP32), else the one-column kernel
+// Default launch shape: the two-column kernel at tau = 1 where it applies
+// (CTAs 64 columns wide for 16-bit storage, 128 for FP32), else the one-column kernel
 // with CTAs 128 columns wide (64 on lattices narrower than 1024), and
 // a band height that makes the grid one full wave of
 // resident CTAs (all bands do the same work, so a partial second wave would
@@ -115,15 +115,15 @@ int store_of(int dtype)
 Shape default_shape(const tf_lbm_params& p, const Geom& G, bool kfield)
 {
     Shape s;
-    // two columns per thread where pairs fit (nx even): it issues fewer
-    // instructions per node than the one-column kernel, which is issue bound.
-    // 16-bit storage uses it at 64 columns per CTA (one warp), FP32 at 128;
-    // FP32 at tau != 1 keeps the one-column kernel (its pulled-population ring
-    // costs the two-column kernel resident warps)
+    // two columns per thread at tau = 1 where pairs fit (nx even): it issues
+    // fewer instructions per node than the one-column kernel, which is issue
+    // bound; 16-bit storage uses it at 64 columns per CTA (one warp), FP32 at
+    // 128.  At tau != 1 the one-column kernel is faster in every storage type
+    // (the two-column kernel's pulled-population ring costs resident warps)
     const int store = store_of(p.dtype);
     const bool om1 = p.tau == 1.0;
     const bool narrow = store == kStoreF16 || store == kStoreBF16;
-    const bool pair = pair_pipeline_ok(G.nx, store) && (narrow || (store == kStoreF32 && om1));
+    const bool pair = pair_pipeline_ok(G.nx, store) && om1;
     s.block_x = pair ? (narrow ? 64 : 128) : (G.nx >= 1024 ? 128 : 64);
     const int strips = (G.nx + s.block_x - 5) / (s.block_x - 4);  // CTAs overlap by 4 columns
     int sms = 152;

@@ -528,11 +528,10 @@ int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32
     int rc = write_table(B, st);
     if (rc) return bail(rc);
 
-    // default shape: the two-column kernel where it applies and a single
-    // handle would take it (16-bit storage, or FP32 with every tau == 1), 64
-    // columns per CTA for 16-bit storage and 128 for FP32; else the
-    // one-column kernel, 64-wide CTAs unless most domains are wide; band
-    // height filling one wave of resident CTAs
+    // default shape: the two-column kernel where it applies and every tau is
+    // 1 (as for a single handle), 64 columns per CTA for 16-bit storage and
+    // 128 for FP32; else the one-column kernel, 64-wide CTAs unless most
+    // domains are wide; band height filling one wave of resident CTAs
     std::vector<int> widths;
     long long nodes = 0;
     for (auto* H : B->hs) {
@@ -542,7 +541,7 @@ int tf_lbm_batch_create(tf_lbm_batch** out, tf_lbm_handle* const* handles, int32
     std::nth_element(widths.begin(), widths.begin() + widths.size() / 2, widths.end());
     tf_lbm_batch_launch L{};
     const bool narrow = B->store == kStoreF16 || B->store == kStoreBF16;
-    L.pipeline = B->pair_ok && (narrow || B->om1) ? kPipePair : kPipeLdg;
+    L.pipeline = B->pair_ok && B->om1 ? kPipePair : kPipeLdg;
     if (L.pipeline == kPipePair) L.block_x = narrow ? 64 : 128;
     else L.block_x = widths[widths.size() / 2] >= 1024 ? 128 : 64;
     const int occ = std::max(1, batch_occupancy(B, L.block_x, L.pipeline));

@@ -340,7 +340,8 @@ def test_bulk_copy_pipeline_needs_nx_multiple_of_8():
     assert p["tau"] == 1.0
     assert sim.launch["pipeline"] == 3  # FP32, tau = 1, nx even: two columns per thread
     assert ThinFilm(p, h0, th, dtype="f16").launch["pipeline"] == 3  # 16-bit, nx even: two columns
-    assert ThinFilm(dict(p, tau=0.8), h0, th).launch["pipeline"] == 1  # FP32, tau != 1: one column
+    assert ThinFilm(dict(p, tau=0.8), h0, th).launch["pipeline"] == 1  # tau != 1: one column
+    assert ThinFilm(dict(p, tau=0.8), h0, th, dtype="f16").launch["pipeline"] == 1
     h1, t1, p1 = inputs.small_random(301, 20, seed=1)
     assert ThinFilm(p1, h1, t1).launch["pipeline"] == 1  # nx odd: one column
     with pytest.raises(L.TfLbmError):
