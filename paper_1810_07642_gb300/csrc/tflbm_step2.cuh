@@ -101,6 +101,25 @@ template <typename V> __device__ __forceinline__ V from_bits(uint32_t u)
 }
 __device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
+// acc += the two stored values of q, each added to its lane in FP32 by the
+// mixed-precision add of sm_100 and later (16-bit operand, FP32 sum, one
+// rounding)
+template <typename SM> __device__ __forceinline__ void mixed_add(float2& acc, typename PairIO<SM>::V q);
+template <> __device__ __forceinline__ void mixed_add<__half>(float2& acc, __half2 q)
+{
+    unsigned short lo, hi;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(bits(q)));
+    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.x) : "h"(lo));
+    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.y) : "h"(hi));
+}
+template <> __device__ __forceinline__ void mixed_add<__nv_bfloat16>(float2& acc, __nv_bfloat162 q)
+{
+    unsigned short lo, hi;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(bits(q)));
+    asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.x) : "h"(lo));
+    asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.y) : "h"(hi));
+}
+
 // The nine pairs of one 3 x 4 stencil window of a shared row triple: for
 // each of the rows n (+y), c, s (-y) the pair at the thread's own columns
 // (x, x+1) and the shifted pairs (x-1, x) and (x+1, x+2).
@@ -264,12 +283,22 @@ __device__ __forceinline__ void pair_collide_store(const Win& P, float2 dh, floa
     } else {
         const V q2 = IO::enc(o2), q3 = IO::enc(o3), q4 = IO::enc(o4), q5 = IO::enc(o5);
         const V q6 = IO::enc(o6), q7 = IO::enc(o7), q8 = IO::enc(o8), q1r = IO::enc(o1);
-        // what the readers reconstruct of l = 2..8 (storage units, exact)
-        const float2 rest = padd(padd(padd(IO::dec(q2), IO::dec(q3)), padd(IO::dec(q4), IO::dec(q5))),
-                                 padd(padd(IO::dec(q6), IO::dec(q7)), IO::dec(q8)));
+        // what the readers reconstruct of l = 2..8 (storage units; each
+        // stored value enters the FP32 sum by a mixed-precision add, which
+        // takes the 16-bit operand as it is: one instruction per value
+        // instead of a conversion and half a paired add)
+        float2 rest = IO::dec(q2);
+        mixed_add<SM>(rest, q3);
+        mixed_add<SM>(rest, q4);
+        mixed_add<SM>(rest, q5);
+        mixed_add<SM>(rest, q6);
+        mixed_add<SM>(rest, q7);
+        mixed_add<SM>(rest, q8);
+        float2 rest1 = rest;
+        mixed_add<SM>(rest1, q1r);
         // the moving populations' total with f_1 unrounded and rounded
         const float2 osum = pfma(padd(rest, o1), pk(C.minv), pk(C.r_sum));
-        const float2 osr = pfma(padd(rest, IO::dec(q1r)), pk(C.minv), pk(C.r_sum));
+        const float2 osr = pfma(rest1, pk(C.minv), pk(C.r_sum));
         // the last residual goes to the finer of the two roundings: the 16-bit
         // one of f_1 - R or the FP32 one of f_0 - href (see collide_store)
         constexpr float kRatio = std::is_same<SM, __half>::value ? 8192.0f : 65536.0f;
